@@ -1,0 +1,25 @@
+"""FP64 CPU oracle for the even-odd Wilson-clover propagator solve.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never calls it, and it shares no code with the CUDA path: the two meet only in
+the seeded arrays of the ``workloads`` module.
+
+The oracle is a plain, slow, direct transcription of the definitions:
+
+* ``gamma``   -- DeGrand-Rossi Dirac matrices and the QDP Gamma(n) index (Sec. II.A).
+* ``lattice`` -- lexicographic <-> QDP cb2 layouts and nearest-neighbour shifts (Sec. II.A).
+* ``dirac``   -- hopping term, clover term and the kappa-normalised operator
+                 M = A - kappa*H of Eq. 5 (isotropic), its even-odd Schur complement and
+                 the true residual.
+* ``solvers`` -- BiCGStab and CG on the normal equations (Sec. II.E, the defaults for
+                 Wilson/clover), and flexible GCR.
+* ``ptc``     -- the gauge-covariant parallel-transport network used as a learned
+                 preconditioner, forward and analytic backward.
+
+Everything is complex128 and operates on whole-lattice arrays in
+lexicographic order (Lt, Lz, Ly, Lx, ...), converting to and from the QDP
+layout at the edges.  Which pins check each function is stated in its
+docstring; functions without a pin say "parity unpinned".
+"""
+from . import gamma, lattice, dirac, solvers, ptc  # noqa: F401

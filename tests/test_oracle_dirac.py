@@ -1,0 +1,165 @@
+"""Pins for the oracle's Wilson-clover operator (Eq. 5, isotropic; Sec. II.A layouts).
+
+Each test checks the oracle against something other than itself: a closed form,
+an identity the operator must satisfy, or the loop-built dense matrix.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dirac
+from oracle import lattice as L
+from oracle.gamma import GAMMA, GAMMA5, sigma
+
+from _dense_ref import dense_matrix, parity_indices
+
+
+def _rand_fermion(dims, seed):
+    return L.from_qdp(W.gaussian_fermion(dims, seed), dims)
+
+
+# --- layout ------------------------------------------------------------------
+
+def test_qdp_roundtrip_and_parity():
+    dims = (4, 2, 6, 4)
+    q = W.gaussian_fermion(dims, 5)
+    lex = L.from_qdp(q, dims)
+    np.testing.assert_array_equal(L.to_qdp(lex, dims), q)
+    # a point source at (x,y,z,t) = (3,1,2,1): parity 1, cb index ((1*6+2)*2+1)*2 + 1
+    ps = W.point_source(dims, 2, 1, site=(3, 1, 2, 1))
+    assert ps[1, 1, 2, 1, 1, 2, 1] == 1.0
+    assert L.from_qdp(ps, dims)[1, 2, 1, 3, 2, 1] == 1.0
+
+
+# --- free field: plane waves are eigenvectors with the closed-form symbol ------
+
+@pytest.mark.parametrize("t_boundary", [-1, 1])
+@pytest.mark.parametrize("n", [(0, 0, 0, 0), (1, 0, 2, 1), (1, 1, 1, 3)])
+def test_free_field_plane_wave(n, t_boundary):
+    dims = (4, 2, 6, 8)
+    kappa, csw = 0.11, 1.3  # F = 0 on the free field, so the clover is the identity
+    U = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    op = dirac.WilsonClover(U, kappa, csw, t_boundary)
+    lx, ly, lz, lt = dims
+    p = [2 * np.pi * n[0] / lx, 2 * np.pi * n[1] / ly, 2 * np.pi * n[2] / lz,
+         (2 * np.pi * n[3] + (np.pi if t_boundary == -1 else 0.0)) / lt]
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+    psi = phase[..., None, None] * u
+    # M(p) = (1 - 2 kappa sum cos p) + 2 i kappa sum gamma_mu sin p_mu
+    a = 1 - 2 * kappa * np.sum(np.cos(p))
+    Mp = a * np.eye(4) + 2j * kappa * sum(GAMMA[m] * np.sin(p[m]) for m in range(4))
+    expect = phase[..., None, None] * (Mp @ u)
+    np.testing.assert_allclose(op.M(psi), expect, atol=1e-13)
+    # eigenvalues a +- 2 i kappa sqrt(sum sin^2), each twice
+    ev = np.linalg.eigvals(Mp)
+    ev = ev[np.argsort(ev.imag)]
+    b = 2 * kappa * np.sqrt(np.sum(np.sin(p) ** 2))
+    np.testing.assert_allclose(ev, np.array([a - 1j * b] * 2 + [a + 1j * b] * 2), atol=1e-13)
+
+
+# --- gamma5-hermiticity (Sec. III.A uses gamma5 S gamma5 = S^+) ------------------
+
+def test_gamma5_hermiticity():
+    dims = (4, 4, 2, 6)
+    op = dirac.from_qdp_problem(W.gauge_links(dims, 0.5, 11), dims, 0.12, 1.7)
+    phi, psi = _rand_fermion(dims, 1), _rand_fermion(dims, 2)
+    lhs = np.vdot(phi, op.M(psi))
+    rhs = np.vdot(dirac.gamma5(op.M(dirac.gamma5(phi))), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # the clover is Hermitian and commutes with gamma5
+    np.testing.assert_allclose(op.A, np.conj(np.swapaxes(op.A, -1, -2)), atol=1e-15)
+    g5 = np.kron(GAMMA5, np.eye(3))
+    np.testing.assert_allclose(op.A @ g5, g5 @ op.A, atol=1e-15)
+    # Schur operator: M_hat^+ = gamma5 M_hat gamma5
+    xe, ye = phi * op.even, psi * op.even
+    assert abs(np.vdot(xe, op.Mhat(ye)) - np.vdot(op.Mhat(xe, dagger=True), ye)) < 1e-12 * np.linalg.norm(xe) * np.linalg.norm(ye)
+
+
+# --- gauge covariance --------------------------------------------------------
+
+def _gauge_transform(U, omega):
+    out = np.empty_like(U)
+    for mu in range(4):
+        out[mu] = np.einsum("...ab,...bc,...dc->...ad", omega, U[mu], L.fwd(omega, mu).conj())
+    return out
+
+
+def test_gauge_covariance():
+    dims = (4, 2, 4, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.6, 3), dims)
+    omega = W.random_su3(dims, 9)
+    Uo = _gauge_transform(U, omega)
+    psi = _rand_fermion(dims, 4)
+    op, opo = dirac.WilsonClover(U, 0.125, 1.1), dirac.WilsonClover(Uo, 0.125, 1.1)
+    rot = lambda f: np.einsum("...ab,...sb->...sa", omega, f)
+    np.testing.assert_allclose(opo.M(rot(psi)), rot(op.M(psi)), atol=1e-12)
+    for mu, nu in dirac.PLANES:
+        f, fo = dirac.field_strength(U, mu, nu), dirac.field_strength(Uo, mu, nu)
+        np.testing.assert_allclose(fo, np.einsum("...ab,...bc,...dc->...ad", omega, f, omega.conj()), atol=1e-12)
+
+
+# --- clover: abelian constant field closed form --------------------------------
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_clover_abelian_constant_field(k):
+    dims = (8, 4, 2, 4)
+    lx = dims[0]
+    B = 2 * np.pi * k / lx
+    U = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    x = np.arange(lx)[None, None, None, :]
+    ph = np.exp(1j * B * x)
+    U[1][..., 0, 0] = ph
+    U[1][..., 1, 1] = ph
+    U[1][..., 2, 2] = np.exp(-2j * B * x)
+    # every xy plaquette is diag(e^{iB}, e^{iB}, e^{-2iB}); F_xy = (P - P^+)/2 minus trace/3
+    d = np.array([np.sin(B), np.sin(B), -np.sin(2 * B)])
+    d = d - d.sum() / 3
+    Fxy = 1j * np.diag(d)
+    for mu, nu in dirac.PLANES:
+        f = dirac.field_strength(U, mu, nu)
+        expect = Fxy if (mu, nu) == (0, 1) else np.zeros((3, 3))
+        np.testing.assert_allclose(f, np.broadcast_to(expect, f.shape), atol=1e-14)
+    kappa, csw = 0.13, 1.9
+    A = dirac.clover_matrix(U, kappa, csw)
+    expectA = np.eye(12) - kappa * csw * np.kron(sigma(0, 1), Fxy)
+    np.testing.assert_allclose(A, np.broadcast_to(expectA, A.shape), atol=1e-14)
+
+
+def test_clover_trivial_limits():
+    dims = (4, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.5, 2), dims)
+    np.testing.assert_allclose(dirac.clover_matrix(U, 0.12, 0.0), np.broadcast_to(np.eye(12), (4, 2, 2, 4, 12, 12)), atol=0)
+    U1 = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    np.testing.assert_allclose(dirac.clover_matrix(U1, 0.12, 1.0), np.broadcast_to(np.eye(12), (4, 2, 2, 4, 12, 12)), atol=1e-15)
+
+
+# --- dense brute force on 2^4 and a small 4^2 x 2^2 ----------------------------
+
+@pytest.mark.parametrize("dims,t_boundary", [((2, 2, 2, 2), -1), ((4, 2, 2, 4), -1), ((2, 4, 2, 2), 1)])
+def test_dense_matrix_matches(dims, t_boundary):
+    Uq = W.gauge_links(dims, 0.7, 21)
+    U = L.gauge_from_qdp(Uq, dims)
+    kappa, csw = 0.12, 1.4
+    op = dirac.WilsonClover(U, kappa, csw, t_boundary)
+    M = dense_matrix(U, dims, kappa, csw, t_boundary)
+    psi = _rand_fermion(dims, 7)
+    np.testing.assert_allclose(op.M(psi).ravel(), M @ psi.ravel(), atol=1e-13)
+    # Schur complement built from dense blocks vs the oracle's M_hat
+    ie, io = parity_indices(dims, 0), parity_indices(dims, 1)
+    Mee, Meo, Moe, Moo = M[np.ix_(ie, ie)], M[np.ix_(ie, io)], M[np.ix_(io, ie)], M[np.ix_(io, io)]
+    Mhat = Mee - Meo @ np.linalg.solve(Moo, Moe)
+    xe = psi * op.even
+    np.testing.assert_allclose(op.Mhat(xe).ravel()[ie], Mhat @ xe.ravel()[ie], atol=1e-12)
+    # dense solve of the full system vs Schur + BiCGStab, and the Schur source
+    b = _rand_fermion(dims, 8)
+    xs = np.linalg.solve(M, b.ravel())
+    bhat = b.ravel()[ie] - Meo @ np.linalg.solve(Moo, b.ravel()[io])
+    np.testing.assert_allclose(op.schur_source(b).ravel()[ie], bhat, atol=1e-12)
+    xe_exact = np.linalg.solve(Mhat, bhat)
+    np.testing.assert_allclose(xs[ie], xe_exact, atol=1e-11)
+    full = np.zeros_like(psi).ravel()
+    full[ie] = xe_exact
+    np.testing.assert_allclose(op.reconstruct(full.reshape(psi.shape), b).ravel(), xs, atol=1e-11)

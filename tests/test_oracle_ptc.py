@@ -1,0 +1,113 @@
+"""Pins for the oracle's parallel-transport network (learned preconditioner)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dirac, ptc
+from oracle import lattice as L
+from oracle.gamma import GAMMA
+
+
+def _field(dims, seed, n=None):
+    q = W.gaussian_fermion(dims, seed)
+    return L.from_qdp(q, dims)
+
+
+def test_transport_adjoint():
+    dims = (4, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.8, 1), dims)
+    phi, psi = _field(dims, 2), _field(dims, 3)
+    for s in range(ptc.NSHIFT):
+        lhs = np.vdot(phi, ptc.transport(U, psi, s))
+        rhs = np.vdot(ptc.transport_adjoint(U, phi, s), psi)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_layer_reproduces_wilson_operator():
+    """A single 1->1 layer with W_0 = 1, W_{+mu} = -kappa(1-gamma_mu), W_{-mu} = -kappa(1+gamma_mu)
+    is the c_sw = 0 Wilson operator 1 - kappa H (pinned separately against closed forms)."""
+    dims = (4, 4, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.5, 6), dims)
+    kappa = 0.12
+    Wt = np.zeros((1, 1, 9, 4, 4), dtype=np.complex128)
+    Wt[0, 0, 0] = np.eye(4)
+    for mu in range(4):
+        Wt[0, 0, 1 + 2 * mu] = -kappa * (np.eye(4) - GAMMA[mu])
+        Wt[0, 0, 2 + 2 * mu] = -kappa * (np.eye(4) + GAMMA[mu])
+    psi = _field(dims, 7)
+    out = ptc.layer_forward(U, Wt, psi[None])[0]
+    np.testing.assert_allclose(out, dirac.WilsonClover(U, kappa, 0.0).M(psi), atol=1e-13)
+
+
+def test_layer_gauge_covariance():
+    dims = (4, 2, 4, 2)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.7, 2), dims)
+    om = W.random_su3(dims, 5)
+    Uo = np.empty_like(U)
+    for mu in range(4):
+        Uo[mu] = np.einsum("...ab,...bc,...dc->...ad", om, U[mu], L.fwd(om, mu).conj())
+    ws = ptc.init_weights((2, 3), seed=1, scale=0.3)
+    x = np.stack([_field(dims, 8), _field(dims, 9)])
+    rot = lambda f: np.einsum("...ab,...sb->...sa", om, f)
+    lhs = ptc.layer_forward(Uo, ws[0], np.stack([rot(c) for c in x]))
+    rhs = np.stack([rot(c) for c in ptc.layer_forward(U, ws[0], x)])
+    np.testing.assert_allclose(lhs, rhs, atol=1e-12)
+
+
+@pytest.mark.parametrize("layer", [0, 1, 3])
+def test_gradient_finite_differences(layer):
+    dims = (2, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.6, 3), dims)
+    ws = ptc.init_weights(ptc.DEFAULT_CHANNELS, seed=2, scale=0.2)
+    rs = [_field(dims, 10), _field(dims, 11)]
+    es = [_field(dims, 12), _field(dims, 13)]
+    _, grads = ptc.loss_and_grad(U, ws, rs, es)
+    rng = np.random.default_rng(layer)
+    h = 1e-6
+    for _ in range(4):
+        idx = tuple(rng.integers(0, n) for n in ws[layer].shape)
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            wp = [w.copy() for w in ws]
+            wm = [w.copy() for w in ws]
+            wp[layer][idx] += h * unit
+            wm[layer][idx] -= h * unit
+            fd = (ptc.loss_and_grad(U, wp, rs, es)[0] - ptc.loss_and_grad(U, wm, rs, es)[0]) / (2 * h)
+            an = grads[layer][idx].real if part == "re" else grads[layer][idx].imag
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (idx, part, fd, an)
+
+
+def test_input_gradient_finite_differences():
+    dims = (2, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.6, 4), dims)
+    ws = ptc.init_weights((2, 3), seed=3, scale=0.3)
+    x = np.stack([_field(dims, 20), _field(dims, 21)])
+    target = ptc.layer_forward(U, ws[0], x) * 0.5 + 0.1
+    loss = lambda xx: float(np.sum(np.abs(ptc.layer_forward(U, ws[0], xx) - target) ** 2))
+    g_out = 2 * (ptc.layer_forward(U, ws[0], x) - target)
+    _, gx = ptc.layer_backward(U, ws[0], x, g_out)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        idx = tuple(rng.integers(0, n) for n in x.shape)
+        for unit, part in ((1.0, "re"), (1j, "im")):
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += h * unit
+            xm[idx] -= h * unit
+            fd = (loss(xp) - loss(xm)) / (2 * h)
+            an = gx[idx].real if part == "re" else gx[idx].imag
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_adam_reduces_loss():
+    dims = (2, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.3, 5), dims)
+    op = dirac.WilsonClover(U, 0.12, 1.0)
+    es = [_field(dims, 30 + k) for k in range(3)]
+    rs = [op.M(e) for e in es]
+    ws = ptc.init_weights(ptc.DEFAULT_CHANNELS, seed=0)
+    l0, g = ptc.loss_and_grad(U, ws, rs, es)
+    state = {}
+    for _ in range(30):
+        ws = ptc.adam_step(ws, g, state, lr=1e-2)
+        l1, g = ptc.loss_and_grad(U, ws, rs, es)
+    assert l1 < 0.5 * l0
