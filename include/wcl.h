@@ -1,0 +1,179 @@
+/*
+ * wcl.h -- C ABI of libwcl, a GB300 (sm_103a) Wilson-clover propagator solver.
+ *
+ * The calls follow the statement of the problem in arXiv:2411.08461:
+ * load a gauge field with kappa and c_sw and build the clover field
+ * (Sec. III.B, "loadGauge ... the clover field is then created"), apply the
+ * fermion matrix (Sec. II.E), and invert it for one or twelve spin-colour
+ * sources, returning the solution, the true residual and the iteration count
+ * (Sec. III.B: 12 inversions per propagator, invertMultiSrcQuda as the
+ * batched form).
+ *
+ * Conventions (Sec. II.A):
+ *   - lattice [Lx, Ly, Lz, Lt], Lx even, every extent >= 2;
+ *   - QDP checkerboard ("cb2") order: parity p = (x+y+z+t) mod 2 first, then
+ *     cb = ((t*Lz + z)*Ly + y)*(Lx/2) + x/2;
+ *   - gauge   [4][2][Lt][Lz][Ly][Lx/2][3][3] complex128 (interleaved re, im),
+ *             U[mu] is the link from s to s + mu_hat, mu = 0..3 <-> x, y, z, t,
+ *             row-column colour order;
+ *   - fermion [2][Lt][Lz][Ly][Lx/2][4][3] complex128, spin then colour;
+ *     several right-hand sides are stored back to back, [nrhs][fermion];
+ *   - DeGrand-Rossi gamma matrices (Chroma convention).
+ *
+ * Operator (Eq. 5, isotropic, multiplied by 2*kappa):
+ *   M = A - kappa * H,
+ *   H psi(s) = sum_mu eta (1 - gamma_mu) U_mu(s) psi(s+mu)
+ *                   + eta (1 + gamma_mu) U_mu(s-mu)^+ psi(s-mu),
+ *   A = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu},
+ *   sigma_{mu nu} = [gamma_mu, gamma_nu]/2, F the traceless anti-Hermitian
+ *   clover-leaf field strength; eta = t_boundary on hops across the time
+ *   boundary (Sec. III.B: t_boundary = -1, antiperiodic), periodic in space.
+ *   The solution of the mass-normalised operator a_t*M of the paper is 2*kappa*x.
+ *
+ * Even-odd (Schur) form used by the solvers and by wcl_apply_Mpc:
+ *   M_hat = A_ee - kappa^2 D_eo A_oo^-1 D_oe.
+ *
+ * Ownership and execution:
+ *   - every d_* pointer is caller-owned, contiguous device memory (e.g. a
+ *     torch tensor's data_ptr()), and must stay valid for the duration of the
+ *     call; the library never frees it;
+ *   - the library owns its internal copies (reordered links, clover, solver
+ *     workspace) and frees them in wcl_destroy;
+ *   - all device work is issued on the stream given to wcl_create; every call
+ *     returns only after its work is complete, so results and info structs are
+ *     valid on return;
+ *   - a context must not be used from two host threads at once.
+ *
+ * Errors: every call returns a wcl_status and never aborts the process.  A
+ * CUDA error is reported as WCL_ERR_CUDA; wcl_last_error() gives the text of
+ * the most recent failure on the calling thread.
+ */
+#ifndef WCL_H
+#define WCL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wcl_ctx wcl_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  WCL_OK = 0,
+  WCL_ERR_INVALID_ARG = 1,  /* bad dims, null pointer, unsupported option */
+  WCL_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  WCL_ERR_OOM = 3,          /* device allocation failed */
+  WCL_ERR_NOT_CONVERGED = 4,/* maxiter reached; x and info hold the best iterate */
+  WCL_ERR_BREAKDOWN = 5,    /* Krylov breakdown persisted after restarts */
+  WCL_ERR_NONFINITE = 6,    /* NaN or Inf in an input or in a residual */
+  WCL_ERR_RECONSTRUCT = 7,  /* a link is not SU(3) to 1e-12: 12-real storage impossible */
+  WCL_ERR_TIMEOUT = 8,      /* a bounded device wait expired */
+  WCL_ERR_NO_GAUGE = 9,     /* wcl_load_gauge has not been called */
+  WCL_ERR_NO_PRECOND = 10   /* learned solver requested without weights */
+} wcl_status;
+
+typedef enum { WCL_F64 = 0, WCL_F32 = 1, WCL_F16 = 2, WCL_BF16 = 3 } wcl_prec;
+
+typedef enum {
+  WCL_BICGSTAB = 0,      /* BiCGStab on M_hat (Sec. II.E: default for clover) */
+  WCL_CGNR = 1,          /* CG on M_hat^+ M_hat (Sec. II.E: CG) */
+  WCL_FGCR_LEARNED = 2   /* flexible GCR on M_hat with the learned preconditioner */
+} wcl_solver;
+
+typedef struct {
+  wcl_solver solver;
+  wcl_prec outer;        /* must be WCL_F64: solution and true residual are FP64 */
+  wcl_prec sloppy;       /* precision of the inner Krylov vectors, links and clover */
+  double tol;            /* target relative true residual ||b - M x|| / ||b|| */
+  int maxiter;           /* total inner iterations per right-hand side */
+  double delta_reliable; /* reliable update when ||r|| < delta * max||r|| since the last one */
+  int restart_on_update; /* 1: restart the Krylov space at every update (defect correction) */
+  int gcr_nkrylov;       /* FGCR restart length */
+  int use_graphs;        /* capture check_every iterations in a CUDA graph */
+  int check_every;       /* iterations between host convergence checks */
+} wcl_solve_params;
+
+typedef struct {
+  int iters;             /* inner iterations */
+  double true_residual;  /* ||b - M x|| / ||b|| in FP64 over the whole lattice */
+  int reliable_updates;  /* FP64 residual replacements */
+  int status;            /* wcl_status of this right-hand side */
+  double seconds;        /* wall time of the whole call */
+} wcl_solve_info;
+
+/* Fill *p with defaults: BiCGStab, outer F64, sloppy F32, tol 1e-10,
+ * maxiter 20000, delta 0.1, no restarts, nkrylov 20, graphs on, check_every 8. */
+void wcl_default_params(wcl_solve_params* p);
+
+/* Human-readable name of a status code (static storage). */
+const char* wcl_status_string(wcl_status s);
+
+/* Text of the most recent error on the calling thread ("" if none). */
+const char* wcl_last_error(void);
+
+/* Create a context for one lattice.
+ *   dims       : {Lx, Ly, Lz, Lt}; Lx even, all >= 2, volume < 2^31 sites.
+ *   t_boundary : +1 periodic or -1 antiperiodic fermion time boundary.
+ *   device     : CUDA device ordinal; made current for every call on ctx.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * The caller owns *out and releases it with wcl_destroy. */
+wcl_status wcl_create(wcl_ctx** out, const int dims[4], int t_boundary, int device, void* cuda_stream);
+
+/* Load a gauge field and build the clover term and its inverse (Sec. III.B).
+ *   d_gauge: device, complex128, QDP layout above; read only.
+ *   kappa  : hopping parameter, csw: clover coefficient (isotropic).
+ * The links are checked to be SU(3) (|U U^+ - 1|, |det U - 1| < 1e-12);
+ * otherwise WCL_ERR_RECONSTRUCT.  Non-finite entries give WCL_ERR_NONFINITE.
+ * The clover field is built from the bare links in FP64, inverted per chiral
+ * 6x6 block in FP64 and stored in every precision. */
+wcl_status wcl_load_gauge(wcl_ctx* ctx, const void* d_gauge, double kappa, double csw);
+
+/* d_out = M d_in on the whole lattice for nrhs fields (QDP layout, complex128),
+ * computed in precision prec (links, clover and spinors stored in prec). */
+wcl_status wcl_apply_D(wcl_ctx* ctx, void* d_out, const void* d_in, wcl_prec prec, int nrhs);
+
+/* d_out_e = M_hat d_in_e (dagger = 0) or M_hat^+ d_in_e (dagger = 1) on the even
+ * half-lattice: each field is [Lt][Lz][Ly][Lx/2][4][3] complex128 (the first
+ * half of a QDP fermion), nrhs of them back to back. */
+wcl_status wcl_apply_Mpc(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, wcl_prec prec, int nrhs, int dagger);
+
+/* Solve M x = b for nrhs right-hand sides (1..12) through the Schur complement.
+ *   d_x, d_b: device, [nrhs][QDP fermion] complex128; d_x is written.
+ *   info    : host array of nrhs entries, filled on return.
+ * Returns WCL_OK when every right-hand side reached params->tol, otherwise the
+ * first failing status (x still holds the best iterate). */
+wcl_status wcl_invert(wcl_ctx* ctx, void* d_x, const void* d_b, int nrhs,
+                      const wcl_solve_params* params, wcl_solve_info* info);
+
+/* Solve on several lattices of different sizes at once: one launch per solver
+ * step covers every lattice and right-hand side (nctx <= 8, same nrhs on each).
+ *   ctxs[i], d_x[i], d_b[i]: the context and the fields of lattice i;
+ *   info: host array of nctx * nrhs entries, lattice-major. */
+wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, const void* const* d_b, int nrhs,
+                            const wcl_solve_params* params, wcl_solve_info* info);
+
+/* Counters for measurement. */
+typedef struct {
+  long long kernel_launches; /* every kernel of this library launched on ctx (graph replays included) */
+  long long dslash_launches; /* fused dslash + clover launches among them */
+  double dslash_ms;          /* summed device time of the timed dslash launches (profiling on) */
+  long long dslash_timed;    /* how many dslash launches were timed */
+  double dslash_bytes;       /* algorithmic bytes of the timed launches */
+  double dslash_flops;       /* algorithmic flops of the timed launches (1320 + 504 per clover site) */
+} wcl_stats;
+
+/* When enabled, every fused dslash launch on ctx is bracketed by CUDA events on
+ * the stream it runs on (also inside captured graphs) and its device time is
+ * accumulated into wcl_stats. */
+wcl_status wcl_set_profiling(wcl_ctx* ctx, int enable);
+
+/* Read (and with reset != 0, afterwards zero) the counters of ctx. */
+wcl_status wcl_get_stats(wcl_ctx* ctx, wcl_stats* out, int reset);
+
+/* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */
+wcl_status wcl_destroy(wcl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCL_H */

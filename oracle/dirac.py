@@ -176,3 +176,63 @@ def apply_Mhat_qdp(op: WilsonClover, psi_even_qdp, dagger=False):
     full[0] = psi_even_qdp
     y = op.Mhat(L.from_qdp(full, op.dims), dagger)
     return L.to_qdp(y, op.dims)[0]
+
+
+# Site-by-site evaluation for lattices too large for whole-array evaluation -------
+
+def _qdp_link(gauge_qdp, dims, mu, c):
+    lx, ly, lz, lt = dims
+    x, y, z, t = (c[0] % lx, c[1] % ly, c[2] % lz, c[3] % lt)
+    p = (x + y + z + t) % 2
+    return gauge_qdp[mu, p, t, z, y, x // 2]
+
+
+def _qdp_psi(psi_qdp, dims, c):
+    lx, ly, lz, lt = dims
+    x, y, z, t = (c[0] % lx, c[1] % ly, c[2] % lz, c[3] % lt)
+    return psi_qdp[(x + y + z + t) % 2, t, z, y, x // 2]
+
+
+def M_at_sites(gauge_qdp, psi_qdp, dims, kappa, csw, sites, t_boundary=-1):
+    """(M psi)(s) for each s = (x, y, z, t) in `sites`, read straight from QDP arrays.
+
+    Same definition as WilsonClover.M (hopping term with the time-boundary sign,
+    clover term from the four leaves), evaluated one site at a time so that it
+    works on lattices of any size.  Pinned against WilsonClover.M.
+    """
+    lx, ly, lz, lt = dims
+    out = []
+    for s in sites:
+        s = tuple(int(v) for v in s)
+
+        def shifted(c, mu, d):
+            c = list(c)
+            c[mu] += d
+            return tuple(c)
+
+        hop = np.zeros((4, 3), dtype=np.complex128)
+        for mu in range(4):
+            cf, cb = shifted(s, mu, 1), shifted(s, mu, -1)
+            ef = t_boundary if (mu == 3 and s[3] == lt - 1) else 1.0
+            eb = t_boundary if (mu == 3 and s[3] == 0) else 1.0
+            uf = _qdp_link(gauge_qdp, dims, mu, s)
+            ub = _qdp_link(gauge_qdp, dims, mu, cb).conj().T
+            hop += ef * (ID4 - GAMMA[mu]) @ (_qdp_psi(psi_qdp, dims, cf) @ uf.T)
+            hop += eb * (ID4 + GAMMA[mu]) @ (_qdp_psi(psi_qdp, dims, cb) @ ub.T)
+        a = np.eye(12, dtype=np.complex128)
+        for mu, nu in PLANES:
+            def link(d, dm, dn):
+                c = list(s)
+                c[mu] += dm
+                c[nu] += dn
+                return _qdp_link(gauge_qdp, dims, d, c)
+            q = (link(mu, 0, 0) @ link(nu, 1, 0) @ link(mu, 0, 1).conj().T @ link(nu, 0, 0).conj().T
+                 + link(nu, 0, 0) @ link(mu, -1, 1).conj().T @ link(nu, -1, 0).conj().T @ link(mu, -1, 0)
+                 + link(mu, -1, 0).conj().T @ link(nu, -1, -1).conj().T @ link(mu, -1, -1) @ link(nu, 0, -1)
+                 + link(nu, 0, -1).conj().T @ link(mu, 0, -1) @ link(nu, 1, -1) @ link(mu, 0, 0).conj().T)
+            f = (q - q.conj().T) / 8.0
+            f = f - np.trace(f) / 3.0 * np.eye(3)
+            a -= kappa * csw * np.kron(sigma(mu, nu), f)
+        val = (a @ _qdp_psi(psi_qdp, dims, s).reshape(12)).reshape(4, 3) - kappa * hop
+        out.append(val)
+    return np.array(out)

@@ -1,0 +1,275 @@
+// Context helpers: errors, workspace, batch geometry, operator launches, profiling.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "context.cuh"
+
+namespace wcl {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+const char* last_error_text() { return g_err; }
+
+wcl_status cuda_fail(cudaError_t e, const char* where) {
+  set_error("%s: %s", where, cudaGetErrorString(e));
+  cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+  return e == cudaErrorMemoryAllocation ? WCL_ERR_OOM : WCL_ERR_CUDA;
+}
+
+wcl_status ws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out) {
+  auto& b = c->ws[name];
+  if (b.bytes < bytes) {
+    if (c->capturing) {
+      set_error("workspace %s requested during graph capture", name.c_str());
+      return WCL_ERR_INVALID_ARG;
+    }
+    if (b.p) {
+      WCL_CUDA(cudaStreamSynchronize(c->stream));
+      WCL_CUDA(cudaFree(b.p));
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    WCL_CUDA(cudaMalloc(&b.p, bytes));
+    WCL_CUDA(cudaMemsetAsync(b.p, 0, bytes, c->stream));
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return WCL_OK;
+}
+
+wcl_status ws_field(const std::vector<wcl_ctx*>& ctxs, const std::string& name, int prec, int nrhs, FieldRef* out) {
+  memset(out, 0, sizeof(*out));
+  for (size_t l = 0; l < ctxs.size(); l++) {
+    wcl_ctx* c = ctxs[l];
+    const long st = c->lat.stride;
+    size_t bytes = (size_t)nrhs * spinor_field_bytes(prec, st);
+    const size_t nbytes = (prec == F16 || prec == BF16) ? (size_t)nrhs * st * sizeof(float) : 0;
+    void* p = nullptr;
+    WCL_CHECK(ws_get(c, name + "#" + std::to_string(prec), bytes + nbytes, &p));
+    out->ptr[l] = p;
+    out->norm[l] = nbytes ? reinterpret_cast<float*>(static_cast<char*>(p) + bytes) : nullptr;
+  }
+  return WCL_OK;
+}
+
+Batch make_batch(const std::vector<wcl_ctx*>& ctxs, int nrhs, int block, int cap) {
+  Batch b;
+  memset(&b, 0, sizeof b);
+  b.nlat = (int)ctxs.size();
+  int blocks = 0;
+  for (int l = 0; l < b.nlat; l++) {
+    const LatticeDevice& L = ctxs[l]->lat;
+    LatGeom& g = b.lat[l];
+    for (int d = 0; d < 4; d++) g.dims[d] = L.dims[d];
+    g.lxh = L.dims[0] / 2;
+    g.vh = (int)L.vh;
+    g.stride = L.stride;
+    g.nrhs = nrhs;
+    long nch = (L.vh + block - 1) / block;
+    if (cap > 0 && nch > cap) nch = cap;
+    g.nchunk = (int)nch;
+    g.block_begin = blocks;
+    g.slot_base = l * nrhs;
+    g.tb = (float)L.tb;
+    blocks += g.nchunk * nrhs;
+  }
+  b.total_blocks = blocks;
+  return b;
+}
+
+static void spinor_site_bytes(int prec, double& sp, double& link, double& clov) {
+  switch (prec) {
+    case F64: sp = 192; link = 96; clov = 576; break;
+    case F32: sp = 96; link = 48; clov = 288; break;
+    default: sp = 52; link = 24; clov = 148; break;
+  }
+}
+
+static wcl_ctx::Timed* prof_begin(wcl_ctx* c) {
+  if (!c->profiling) return nullptr;
+  if (c->ev_used == c->ev_pool.size()) {
+    wcl_ctx::Timed t;
+    if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(t);
+  }
+  wcl_ctx::Timed* t = &c->ev_pool[c->ev_used++];
+  cudaEventRecord(t->a, c->stream);
+  return t;
+}
+
+wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
+                  const FieldRef* x, int out_parity, bool dagger, CloverSel post, CloverSel pre, Coef alpha,
+                  Coef beta, const int* active) {
+  wcl_ctx* c0 = ctxs[0];
+  const int block = c0->dslash_block[prec];
+  DslashArgs a;
+  memset(&a, 0, sizeof a);
+  a.b = make_batch(ctxs, nrhs, block, 0);
+  a.out = out;
+  a.in = in;
+  if (x) a.x = *x;
+  a.out_parity = out_parity;
+  a.active = active;
+  double sites = 0;
+  for (size_t l = 0; l < ctxs.size(); l++) {
+    const LatticeDevice& L = ctxs[l]->lat;
+    a.gauge[l][0] = L.gauge[prec][0];
+    a.gauge[l][1] = L.gauge[prec][1];
+    const int p = out_parity;
+    if (post) {
+      a.cpost[l] = post == CL_A ? L.clov[prec][p] : L.clovinv[prec][p];
+      a.cpost_norm[l] = post == CL_A ? L.clov_norm[prec * 2 + p] : L.clovinv_norm[prec * 2 + p];
+    }
+    if (pre) {
+      a.cpre[l] = pre == CL_A ? L.clov[prec][p] : L.clovinv[prec][p];
+      a.cpre_norm[l] = pre == CL_A ? L.clov_norm[prec * 2 + p] : L.clovinv_norm[prec * 2 + p];
+    }
+    a.alpha[l] = coef_value(alpha, L.kappa);
+    a.beta[l] = coef_value(beta, L.kappa);
+    sites += (double)L.vh * nrhs;
+  }
+  int mode = 0;
+  if (post) mode |= MODE_POST;
+  if (x) mode |= MODE_XPAY;
+  if (x && pre) mode |= MODE_PRE;
+  wcl_ctx::Timed* t = prof_begin(c0);
+  cudaError_t e;
+  switch (prec) {
+    case F64: e = launch_dslash<F64>(a, dagger, mode, block, c0->stream); break;
+    case F32: e = launch_dslash<F32>(a, dagger, mode, block, c0->stream); break;
+    case F16: e = launch_dslash<F16>(a, dagger, mode, block, c0->stream); break;
+    default: e = launch_dslash<BF16>(a, dagger, mode, block, c0->stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
+  count_launch(c0, true);
+  if (t) {
+    cudaEventRecord(t->b, c0->stream);
+    double sp, lk, cl;
+    spinor_site_bytes(prec, sp, lk, cl);
+    double per = 8 * lk + 2 * sp + (post ? cl : 0) + (x ? sp : 0) + (x && pre ? cl : 0);
+    // links and clover are shared by the right-hand sides of a site
+    double per_site_shared = 8 * lk + (post ? cl : 0) + (x && pre ? cl : 0);
+    double per_rhs = per - per_site_shared;
+    double base_sites = sites / nrhs;
+    t->bytes = base_sites * per_site_shared + sites * per_rhs;
+    t->flops = sites * (1320.0 + ((post || (x && pre)) ? 504.0 : 0.0) + (x ? 48.0 : 0.0));
+  }
+  return WCL_OK;
+}
+
+wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out,
+                        const FieldRef& x, int parity, CloverSel which, const int* active) {
+  wcl_ctx* c0 = ctxs[0];
+  const int block = 128;
+  CloverArgs a;
+  memset(&a, 0, sizeof a);
+  a.b = make_batch(ctxs, nrhs, block, 0);
+  a.out = out;
+  a.x = x;
+  a.active = active;
+  for (size_t l = 0; l < ctxs.size(); l++) {
+    const LatticeDevice& L = ctxs[l]->lat;
+    a.c[l] = which == CL_A ? L.clov[prec][parity] : L.clovinv[prec][parity];
+    a.c_norm[l] = which == CL_A ? L.clov_norm[prec * 2 + parity] : L.clovinv_norm[prec * 2 + parity];
+  }
+  cudaError_t e;
+  switch (prec) {
+    case F64: e = launch_clover<F64>(a, block, c0->stream); break;
+    case F32: e = launch_clover<F32>(a, block, c0->stream); break;
+    case F16: e = launch_clover<F16>(a, block, c0->stream); break;
+    default: e = launch_clover<BF16>(a, block, c0->stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "clover launch");
+  count_launch(c0);
+  return WCL_OK;
+}
+
+wcl_status apply_mhat(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out_e,
+                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active) {
+  // tmp_o = A_oo^-1 D_oe in_e
+  WCL_CHECK(dslash(ctxs, prec, nrhs, tmp_o, in_e, nullptr, 1, dagger, CL_AINV, CL_NONE, C_ONE, C_ZERO, active));
+  // out_e = A_ee in_e - kappa^2 D_eo tmp_o
+  WCL_CHECK(dslash(ctxs, prec, nrhs, out_e, tmp_o, &in_e, 0, dagger, CL_NONE, CL_A, C_MKAPPA2, C_ONE, active));
+  return WCL_OK;
+}
+
+template <int PO, int PI>
+static cudaError_t run_convert(const Batch& b, const FieldRef& out, const FieldRef& in, const int* active, int block,
+                               cudaStream_t st) {
+  Convert<PO, PI> f;
+  f.out = out;
+  f.in = in;
+  return run_map(b, f, active, block, st);
+}
+
+wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrhs, const FieldRef& out,
+                   const FieldRef& in, const int* active) {
+  wcl_ctx* c0 = ctxs[0];
+  const int block = c0->blas_block;
+  Batch b = make_batch(ctxs, nrhs, block, RED_MAXCH);
+  cudaError_t e = cudaErrorInvalidValue;
+  const int key = pout * 4 + pin;
+  switch (key) {
+    case F32 * 4 + F64: e = run_convert<F32, F64>(b, out, in, active, block, c0->stream); break;
+    case F16 * 4 + F64: e = run_convert<F16, F64>(b, out, in, active, block, c0->stream); break;
+    case BF16 * 4 + F64: e = run_convert<BF16, F64>(b, out, in, active, block, c0->stream); break;
+    case F64 * 4 + F32: e = run_convert<F64, F32>(b, out, in, active, block, c0->stream); break;
+    case F64 * 4 + F16: e = run_convert<F64, F16>(b, out, in, active, block, c0->stream); break;
+    case F64 * 4 + BF16: e = run_convert<F64, BF16>(b, out, in, active, block, c0->stream); break;
+    case F64 * 4 + F64: e = run_convert<F64, F64>(b, out, in, active, block, c0->stream); break;
+    case F32 * 4 + F32: e = run_convert<F32, F32>(b, out, in, active, block, c0->stream); break;
+    case F16 * 4 + F16: e = run_convert<F16, F16>(b, out, in, active, block, c0->stream); break;
+    case BF16 * 4 + BF16: e = run_convert<BF16, BF16>(b, out, in, active, block, c0->stream); break;
+    default: set_error("conversion %d -> %d not instantiated", pin, pout); return WCL_ERR_INVALID_ARG;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "convert launch");
+  count_launch(c0);
+  return WCL_OK;
+}
+
+static void accum(wcl_ctx* c, size_t from, size_t to) {
+  for (size_t k = from; k < to; k++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[k].a, c->ev_pool[k].b) == cudaSuccess) {
+      c->dslash_ms += ms;
+      c->dslash_timed++;
+      c->dslash_bytes += c->ev_pool[k].bytes;
+      c->dslash_flops += c->ev_pool[k].flops;
+    } else {
+      cudaGetLastError();
+    }
+  }
+}
+
+void profile_flush(wcl_ctx* c, size_t from) {
+  if (c->ev_used > from) accum(c, from, c->ev_used);
+  c->ev_used = from;
+}
+
+wcl_status hws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out) {
+  auto& b = c->hws[name];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      WCL_CUDA(cudaStreamSynchronize(c->stream));
+      WCL_CUDA(cudaFreeHost(b.p));
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    WCL_CUDA(cudaMallocHost(&b.p, bytes));
+    memset(b.p, 0, bytes);
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return WCL_OK;
+}
+
+void profile_accum_range(wcl_ctx* c, size_t from, size_t to) { accum(c, from, to); }
+
+}  // namespace wcl

@@ -1,0 +1,130 @@
+// Library context: device data of one lattice, named workspace buffers, the
+// internal work stream, profiling events and launch counters; plus the helpers
+// that build batch geometry and launch the fused operator kernels.
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/wcl.h"
+#include "blas.cuh"
+#include "dslash.cuh"
+#include "fields.cuh"
+
+struct wcl_ctx {
+  int device = 0;
+  cudaStream_t user_stream = nullptr;  // caller's stream (may be the legacy default)
+  cudaStream_t stream = nullptr;       // internal non-blocking stream all work runs on
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  wcl::LatticeDevice lat;
+  struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::map<std::string, Buf> ws;   // workspace, grown on demand, freed in wcl_destroy
+  std::map<std::string, Buf> hws;  // pinned host staging
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;  // pinned
+
+  // counters and profiling
+  long long kernel_launches = 0, dslash_launches = 0, dslash_timed = 0;
+  double dslash_ms = 0, dslash_bytes = 0, dslash_flops = 0;
+  bool profiling = false;
+  struct Timed {
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  std::vector<Timed> ev_pool;
+  size_t ev_used = 0;
+  bool capturing = false;
+  long long capture_launches = 0, capture_dslash = 0;
+
+  // launch shapes (picked by the tuner on first use)
+  int dslash_block[4] = {128, 128, 128, 128};
+  int blas_block = 256;
+};
+
+namespace wcl {
+
+void set_error(const char* fmt, ...);
+wcl_status cuda_fail(cudaError_t e, const char* where);
+
+#define WCL_CUDA(call)                                       \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);      \
+  } while (0)
+#define WCL_CHECK(call)                  \
+  do {                                   \
+    wcl_status _s = (call);              \
+    if (_s != WCL_OK) return _s;         \
+  } while (0)
+
+// named workspace buffer of at least `bytes`; zero-filled when (re)allocated
+wcl_status ws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out);
+
+// one field of precision prec with nrhs right-hand sides on every lattice of a batch
+wcl_status ws_field(const std::vector<wcl_ctx*>& ctxs, const std::string& name, int prec, int nrhs, FieldRef* out);
+
+// batch geometry for a launch with `block` threads; cap limits blocks per slice (grid-stride)
+Batch make_batch(const std::vector<wcl_ctx*>& ctxs, int nrhs, int block, int cap);
+
+// counts one launch (or, under graph capture, one captured node)
+inline void count_launch(wcl_ctx* c, bool is_dslash = false) {
+  if (c->capturing) {
+    c->capture_launches++;
+    c->capture_dslash += is_dslash;
+  } else {
+    c->kernel_launches++;
+    c->dslash_launches += is_dslash;
+  }
+}
+
+// coefficient selector for the per-lattice alpha / beta of the fused kernels
+enum Coef { C_ZERO, C_ONE, C_KAPPA, C_MKAPPA, C_MKAPPA2 };
+inline double coef_value(Coef c, double kappa) {
+  switch (c) {
+    case C_ZERO: return 0.0;
+    case C_ONE: return 1.0;
+    case C_KAPPA: return kappa;
+    case C_MKAPPA: return -kappa;
+    case C_MKAPPA2: return -kappa * kappa;
+  }
+  return 0.0;
+}
+enum CloverSel { CL_NONE = 0, CL_A = 1, CL_AINV = 2 };
+
+// out_parity field = C_post(alpha D in + beta C_pre x) on all lattices of the batch
+wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
+                  const FieldRef* x, int out_parity, bool dagger, CloverSel post, CloverSel pre, Coef alpha,
+                  Coef beta, const int* active);
+// out = C x on parity `parity`
+wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out,
+                        const FieldRef& x, int parity, CloverSel which, const int* active);
+// M_hat (or its adjoint) in precision prec: out_e = A_ee in_e - kappa^2 D_eo A_oo^-1 D_oe in_e
+wcl_status apply_mhat(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out_e,
+                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active);
+// precision conversion of a parity field
+wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrhs, const FieldRef& out,
+                   const FieldRef& in, const int* active);
+
+// per-precision instantiations (defined in dslash_<prec>.cu)
+template <int P>
+cudaError_t launch_dslash(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st);
+template <int P>
+cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
+
+// caller-owned QDP fields of a solve, one pointer per lattice
+struct SolveIO {
+  void* const* d_x;
+  const void* const* d_b;
+};
+
+// accumulate the device times of profiled launches [from, used) and release them
+// (call after a stream sync); profile_accum_range keeps them (graph-owned events)
+void profile_flush(wcl_ctx* c, size_t from = 0);
+void profile_accum_range(wcl_ctx* c, size_t from, size_t to);
+// pinned host buffer, grown on demand
+wcl_status hws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out);
+
+}  // namespace wcl

@@ -1,0 +1,257 @@
+// Fused even-odd Wilson hopping term + clover (Eq. 5, isotropic):
+//
+//   out = C_post ( alpha * D_{p,1-p} in  +  beta * C_pre x )
+//
+// on output parity p, for every (lattice, rhs) slice of a batch.  D is the
+// hopping term H restricted to (out parity p, in parity 1-p):
+//   D psi(s) = sum_mu eta (1 - g_mu) U_mu(s) psi(s+mu) + eta (1 + g_mu) U_mu(s-mu)^+ psi(s-mu)
+// and with DAG the projector signs are swapped (gamma5 D gamma5 = D^+).
+// C_post / C_pre are clover blocks (A or A^-1) of parity p, or absent.
+//
+// One thread owns one output site.  Per direction the neighbour spinor is
+// spin-projected to a half spinor (2 spins x 3 colours), multiplied by the link
+// (or its adjoint), and the 4-spinor is rebuilt while accumulating.  The
+// DeGrand-Rossi projections, written for (1 + s*gamma_mu):
+//   mu=x: h0 = p0 + s i p3, h1 = p1 + s i p2;  rows 2,3 = -s i h1, -s i h0
+//   mu=y: h0 = p0 - s p3,   h1 = p1 + s p2;    rows 2,3 =  s h1,  -s h0
+//   mu=z: h0 = p0 + s i p2, h1 = p1 - s i p3;  rows 2,3 = -s i h0,  s i h1
+//   mu=t: h0 = p0 + s p2,   h1 = p1 + s p3;    rows 2,3 =  s h0,   s h1
+#pragma once
+#include "internal.cuh"
+
+namespace wcl {
+
+enum DslashMode { MODE_POST = 1, MODE_XPAY = 2, MODE_PRE = 4 };
+
+struct DslashArgs {
+  Batch b;
+  FieldRef out, in, x;
+  const void* gauge[MAXLAT][2];  // per parity: [mu][chunk][stride]
+  const void* cpost[MAXLAT];
+  const float* cpost_norm[MAXLAT];
+  const void* cpre[MAXLAT];
+  const float* cpre_norm[MAXLAT];
+  double alpha[MAXLAT], beta[MAXLAT];
+  int out_parity;
+  const int* active;  // per slot; null = every slice active
+};
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const cpx<R> p[12], cpx<R> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if (MU == 0) {
+      h[c] = (S > 0) ? p0 + ti(p3) : p0 - ti(p3);
+      h[3 + c] = (S > 0) ? p1 + ti(p2) : p1 - ti(p2);
+    } else if (MU == 1) {
+      h[c] = (S > 0) ? p0 - p3 : p0 + p3;
+      h[3 + c] = (S > 0) ? p1 + p2 : p1 - p2;
+    } else if (MU == 2) {
+      h[c] = (S > 0) ? p0 + ti(p2) : p0 - ti(p2);
+      h[3 + c] = (S > 0) ? p1 - ti(p3) : p1 + ti(p3);
+    } else {
+      h[c] = (S > 0) ? p0 + p2 : p0 - p2;
+      h[3 + c] = (S > 0) ? p1 + p3 : p1 - p3;
+    }
+  }
+}
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct_acc(cpx<R> acc[12], const cpx<R> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<R> h0 = h[c], h1 = h[3 + c];
+    acc[c] = acc[c] + h0;
+    acc[3 + c] = acc[3 + c] + h1;
+    if (MU == 0) {
+      acc[6 + c] = (S > 0) ? acc[6 + c] - ti(h1) : acc[6 + c] + ti(h1);
+      acc[9 + c] = (S > 0) ? acc[9 + c] - ti(h0) : acc[9 + c] + ti(h0);
+    } else if (MU == 1) {
+      acc[6 + c] = (S > 0) ? acc[6 + c] + h1 : acc[6 + c] - h1;
+      acc[9 + c] = (S > 0) ? acc[9 + c] - h0 : acc[9 + c] + h0;
+    } else if (MU == 2) {
+      acc[6 + c] = (S > 0) ? acc[6 + c] - ti(h0) : acc[6 + c] + ti(h0);
+      acc[9 + c] = (S > 0) ? acc[9 + c] + ti(h1) : acc[9 + c] - ti(h1);
+    } else {
+      acc[6 + c] = (S > 0) ? acc[6 + c] + h0 : acc[6 + c] - h0;
+      acc[9 + c] = (S > 0) ? acc[9 + c] + h1 : acc[9 + c] - h1;
+    }
+  }
+}
+
+// uh = U h (ADJ = false) or U^+ h (ADJ = true), for both half-spinor components
+template <bool ADJ, typename R>
+__device__ __forceinline__ void link_mul(const cpx<R> u[3][3], const cpx<R> h[6], cpx<R> o[6], R sign) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cpx<R> acc = {0, 0};
+#pragma unroll
+      for (int bb = 0; bb < 3; bb++) {
+        if (ADJ)
+          cfma_conj(acc, u[bb][a], h[3 * k + bb]);
+        else
+          cfma(acc, u[a][bb], h[3 * k + bb]);
+      }
+      o[3 * k + a] = sign * acc;
+    }
+  }
+}
+
+template <int P, int MU, bool DAG>
+__device__ __forceinline__ void hop_dir(cpx<typename Traits<P>::R> acc[12], const void* in, const float* in_norm,
+                                        const void* g_here, const void* g_there, long stride, long i, long jf,
+                                        long jb, typename Traits<P>::R sf, typename Traits<P>::R sb) {
+  using R = typename Traits<P>::R;
+  constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF*gamma
+  constexpr int SB = -SF;
+  cpx<R> psi[12], h[6], uh[6], u[3][3];
+  // forward: U_mu(s) psi(s + mu)
+  SpinorIO<P>::load(psi, in, in_norm, stride, jf);
+  LinkIO<P>::load(u, g_here, stride, i, MU);
+  project<MU, SF>(psi, h);
+  link_mul<false>(u, h, uh, sf);
+  reconstruct_acc<MU, SF>(acc, uh);
+  // backward: U_mu(s - mu)^+ psi(s - mu)
+  SpinorIO<P>::load(psi, in, in_norm, stride, jb);
+  LinkIO<P>::load(u, g_there, stride, jb, MU);
+  project<MU, SB>(psi, h);
+  link_mul<true>(u, h, uh, sb);
+  reconstruct_acc<MU, SB>(acc, uh);
+}
+
+template <int P, bool DAG, int MODE>
+__global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ DslashArgs a) {
+  using R = typename Traits<P>::R;
+  const Slice s = find_slice(a.b, blockIdx.x);
+  if (a.active && !a.active[s.slot]) return;
+  const LatGeom& g = a.b.lat[s.l];
+  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
+  if (i >= g.vh) return;
+  const long stride = g.stride;
+  const int p = a.out_parity;
+
+  // coordinates of the output site
+  const int lxh = g.lxh, Lx = g.dims[0], Ly = g.dims[1], Lz = g.dims[2], Lt = g.dims[3];
+  const int xh = (int)(i % lxh);
+  int rem = (int)(i / lxh);
+  const int y = rem % Ly;
+  rem /= Ly;
+  const int z = rem % Lz;
+  const int t = rem / Lz;
+  const int x = 2 * xh + ((p + y + z + t) & 1);
+  const long row = i - xh;
+  const long plane = (long)lxh * Ly, vol3 = plane * Lz;
+
+  const void* in = rhs_ptr<P>(a.in, s.l, s.rhs, stride);
+  const float* in_norm = rhs_norm(a.in, s.l, s.rhs, stride);
+  const void* g_here = a.gauge[s.l][p];
+  const void* g_there = a.gauge[s.l][1 - p];
+
+  cpx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {0, 0};
+
+  {
+    const long jf = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
+    const long jb = row + ((x == 0 ? Lx - 1 : x - 1) >> 1);
+    hop_dir<P, 0, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb, R(1), R(1));
+  }
+  {
+    const long jf = (y + 1 == Ly) ? i - (long)(Ly - 1) * lxh : i + lxh;
+    const long jb = (y == 0) ? i + (long)(Ly - 1) * lxh : i - lxh;
+    hop_dir<P, 1, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb, R(1), R(1));
+  }
+  {
+    const long jf = (z + 1 == Lz) ? i - (long)(Lz - 1) * plane : i + plane;
+    const long jb = (z == 0) ? i + (long)(Lz - 1) * plane : i - plane;
+    hop_dir<P, 2, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb, R(1), R(1));
+  }
+  {
+    const long jf = (t + 1 == Lt) ? i - (long)(Lt - 1) * vol3 : i + vol3;
+    const long jb = (t == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3;
+    const R sf = (t + 1 == Lt) ? R(g.tb) : R(1);
+    const R sb = (t == 0) ? R(g.tb) : R(1);
+    hop_dir<P, 3, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb, sf, sb);
+  }
+
+  const R alpha = R(a.alpha[s.l]);
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
+
+  if (MODE & MODE_XPAY) {
+    cpx<R> xv[12];
+    SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, s.rhs, stride), rhs_norm(a.x, s.l, s.rhs, stride), stride, i);
+    const R beta = R(a.beta[s.l]);
+    if (MODE & MODE_PRE) {
+      cpx<R> cx[12];
+      CloverIO<P>::apply(cx, xv, a.cpre[s.l], a.cpre_norm[s.l], stride, i);
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * cx[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
+    }
+  }
+  if (MODE & MODE_POST) {
+    cpx<R> y2[12];
+    CloverIO<P>::apply(y2, acc, a.cpost[s.l], a.cpost_norm[s.l], stride, i);
+    SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, s.rhs, stride), rhs_norm(a.out, s.l, s.rhs, stride), stride, i);
+  } else {
+    SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, s.rhs, stride), rhs_norm(a.out, s.l, s.rhs, stride), stride, i);
+  }
+}
+
+// Clover-only: out = C x  (used for A_oo^-1 b_o and stand-alone clover applies).
+struct CloverArgs {
+  Batch b;
+  FieldRef out, x;
+  const void* c[MAXLAT];
+  const float* c_norm[MAXLAT];
+  const int* active;
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) clover_kernel(const __grid_constant__ CloverArgs a) {
+  using R = typename Traits<P>::R;
+  const Slice s = find_slice(a.b, blockIdx.x);
+  if (a.active && !a.active[s.slot]) return;
+  const LatGeom& g = a.b.lat[s.l];
+  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
+  if (i >= g.vh) return;
+  cpx<R> xv[12], y[12];
+  SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, s.rhs, g.stride), rhs_norm(a.x, s.l, s.rhs, g.stride), g.stride, i);
+  CloverIO<P>::apply(y, xv, a.c[s.l], a.c_norm[s.l], g.stride, i);
+  SpinorIO<P>::store(y, rhs_ptr_w<P>(a.out, s.l, s.rhs, g.stride), rhs_norm(a.out, s.l, s.rhs, g.stride), g.stride, i);
+}
+
+// host-side launchers (one instantiation set per precision translation unit)
+template <int P>
+cudaError_t launch_dslash(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st);
+template <int P>
+cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
+
+#define WCL_DEFINE_DSLASH_LAUNCHERS(P)                                                              \
+  template <>                                                                                       \
+  cudaError_t launch_dslash<P>(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st) { \
+    dim3 grid(a.b.total_blocks), blk(block);                                                        \
+    switch (mode | (dagger ? 8 : 0)) {                                                              \
+      case MODE_POST: dslash_kernel<P, false, MODE_POST><<<grid, blk, 0, st>>>(a); break;            \
+      case MODE_POST | 8: dslash_kernel<P, true, MODE_POST><<<grid, blk, 0, st>>>(a); break;        \
+      case MODE_XPAY | MODE_PRE: dslash_kernel<P, false, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
+      case MODE_XPAY | MODE_PRE | 8: dslash_kernel<P, true, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
+      case MODE_XPAY: dslash_kernel<P, false, MODE_XPAY><<<grid, blk, 0, st>>>(a); break;            \
+      case MODE_XPAY | MODE_POST: dslash_kernel<P, false, MODE_XPAY | MODE_POST><<<grid, blk, 0, st>>>(a); break; \
+      default: return cudaErrorInvalidValue;                                                        \
+    }                                                                                               \
+    return cudaGetLastError();                                                                      \
+  }                                                                                                 \
+  template <>                                                                                       \
+  cudaError_t launch_clover<P>(const CloverArgs& a, int block, cudaStream_t st) {                   \
+    clover_kernel<P><<<a.b.total_blocks, block, 0, st>>>(a);                                        \
+    return cudaGetLastError();                                                                      \
+  }
+
+}  // namespace wcl

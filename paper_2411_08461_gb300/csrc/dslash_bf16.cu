@@ -1,0 +1,6 @@
+// Fused dslash + clover kernels, BF16 storage.
+#include "dslash.cuh"
+
+namespace wcl {
+WCL_DEFINE_DSLASH_LAUNCHERS(BF16)
+}  // namespace wcl

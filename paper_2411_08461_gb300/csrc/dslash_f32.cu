@@ -1,0 +1,6 @@
+// Fused dslash + clover kernels, F32 storage.
+#include "dslash.cuh"
+
+namespace wcl {
+WCL_DEFINE_DSLASH_LAUNCHERS(F32)
+}  // namespace wcl

@@ -1,0 +1,403 @@
+// Mixed-precision Krylov driver on the Schur operator M_hat = A_ee - kappa^2 D_eo A_oo^-1 D_oe.
+//
+//   * source:        b_hat = b_e + kappa D_eo A_oo^-1 b_o            (FP64)
+//   * inner solver:  BiCGStab or CGNR in the sloppy precision S with the
+//                    coefficients computed on the device; check_every
+//                    iterations are launched (or replayed as one CUDA graph)
+//                    between host convergence checks
+//   * reliable update (residual replacement, Sleijpen & van der Vorst 1996):
+//                    when ||r|| < delta * max ||r|| since the last update, or
+//                    at apparent convergence: x += x_s, r = b_hat - M_hat x in
+//                    FP64, r_sloppy = r
+//   * finish:        x_o = A_oo^-1 (b_o + kappa D_oe x_e) and the true residual
+//                    ||b - M x|| / ||b|| on the whole lattice in FP64.
+// Every (lattice, rhs) slice keeps its own coefficients and is masked out of
+// every launch once it has converged.
+#pragma once
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "context.cuh"
+
+namespace wcl {
+
+template <int S>
+struct KrylovSolver {
+  static constexpr int X = (S == F64) ? F64 : F32;  // precision of the sloppy solution accumulator
+  std::vector<wcl_ctx*> ctxs;
+  wcl_ctx* c0 = nullptr;
+  int nrhs = 0, nslot = 0;
+  wcl_solve_params prm;
+  bool cg = false;
+
+  FieldRef b_e, b_o, bhat, x, x_o, r64, tmp64;  // FP64
+  FieldRef r, rhat, p, v, t, tmp;               // sloppy
+  FieldRef xs;                                  // accumulator
+  Scalars* d_sc = nullptr;
+  Scalars* h_sc = nullptr;
+  int* d_active = nullptr;
+  int* h_active = nullptr;
+  int* d_upd = nullptr;
+  int* h_upd = nullptr;
+  double* d_part = nullptr;
+  unsigned* d_cnt = nullptr;
+  Batch bb;  // geometry of the BLAS / reduction launches
+  int blk = 256;
+
+  std::vector<double> stop2, r2max;
+  std::vector<int> iters, updates, restarts, status;
+
+  cudaGraphExec_t gexec = nullptr;
+  long long g_launches = 0, g_dslash = 0;
+  size_t g_ev0 = 0, g_ev1 = 0;
+
+  wcl_status alloc() {
+    WCL_CHECK(ws_field(ctxs, "b_e", F64, nrhs, &b_e));
+    WCL_CHECK(ws_field(ctxs, "b_o", F64, nrhs, &b_o));
+    WCL_CHECK(ws_field(ctxs, "bhat", F64, nrhs, &bhat));
+    WCL_CHECK(ws_field(ctxs, "x", F64, nrhs, &x));
+    WCL_CHECK(ws_field(ctxs, "x_o", F64, nrhs, &x_o));
+    WCL_CHECK(ws_field(ctxs, "r64", F64, nrhs, &r64));
+    WCL_CHECK(ws_field(ctxs, "tmp64", F64, nrhs, &tmp64));
+    WCL_CHECK(ws_field(ctxs, "r", S, nrhs, &r));
+    WCL_CHECK(ws_field(ctxs, "rhat", S, nrhs, &rhat));
+    WCL_CHECK(ws_field(ctxs, "p", S, nrhs, &p));
+    WCL_CHECK(ws_field(ctxs, "v", S, nrhs, &v));
+    WCL_CHECK(ws_field(ctxs, "t", S, nrhs, &t));
+    WCL_CHECK(ws_field(ctxs, "tmp", S, nrhs, &tmp));
+    WCL_CHECK(ws_field(ctxs, "xs", X, nrhs, &xs));
+    void* q;
+    WCL_CHECK(ws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
+    d_sc = static_cast<Scalars*>(q);
+    WCL_CHECK(ws_get(c0, "active", sizeof(int) * 2 * nslot, &q));
+    d_active = static_cast<int*>(q);
+    d_upd = d_active + nslot;
+    WCL_CHECK(ws_get(c0, "partials", sizeof(double) * nslot * RED_MAXCH * 4, &q));
+    d_part = static_cast<double*>(q);
+    WCL_CHECK(ws_get(c0, "counters", sizeof(unsigned) * nslot, &q));
+    d_cnt = static_cast<unsigned*>(q);
+    WCL_CHECK(hws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
+    h_sc = static_cast<Scalars*>(q);
+    WCL_CHECK(hws_get(c0, "active", sizeof(int) * 2 * nslot, &q));
+    h_active = static_cast<int*>(q);
+    h_upd = h_active + nslot;
+    return WCL_OK;
+  }
+
+  // zero one field on every lattice
+  wcl_status zero(const FieldRef& f, int prec) {
+    for (size_t l = 0; l < ctxs.size(); l++) {
+      const long st = ctxs[l]->lat.stride;
+      size_t bytes = (size_t)nrhs * spinor_field_bytes(prec, st);
+      if (prec == F16 || prec == BF16) bytes += (size_t)nrhs * st * sizeof(float);
+      WCL_CUDA(cudaMemsetAsync(f.ptr[l], 0, bytes, c0->stream));
+    }
+    return WCL_OK;
+  }
+
+  template <int NR, typename F>
+  wcl_status reduce(const F& f, const int* mask) {
+    cudaError_t e = run_reduce<NR>(bb, f, mask, d_part, d_cnt, d_sc, blk, c0->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+    count_launch(c0);
+    return WCL_OK;
+  }
+  template <typename F>
+  wcl_status map(const F& f, const int* mask) {
+    cudaError_t e = run_map(bb, f, mask, blk, c0->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "map launch");
+    count_launch(c0);
+    return WCL_OK;
+  }
+
+  wcl_status sync_scalars() {
+    WCL_CUDA(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scalars) * nslot, cudaMemcpyDeviceToHost, c0->stream));
+    WCL_CUDA(cudaStreamSynchronize(c0->stream));
+    return WCL_OK;
+  }
+  wcl_status push_masks() {
+    WCL_CUDA(cudaMemcpyAsync(d_active, h_active, sizeof(int) * 2 * nslot, cudaMemcpyHostToDevice, c0->stream));
+    return WCL_OK;
+  }
+
+  // ---- one inner iteration (all active slices) -------------------------------
+  wcl_status iteration() {
+    if (!cg) {
+      WCL_CHECK(map(BicgP<S>{r, p, v, d_sc}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active));
+      WCL_CHECK(reduce<2>(BicgAlpha<S>{rhat, v}, d_active));
+      WCL_CHECK(map(BicgS<S>{r, v, d_sc}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, false, d_active));
+      WCL_CHECK(reduce<3>(BicgOmega<S>{t, r}, d_active));
+      WCL_CHECK(reduce<3>(BicgUpdate<S, X>{xs, p, r, t, rhat, d_sc}, d_active));
+    } else {
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, true, d_active));  // z = M^+ r
+      WCL_CHECK(reduce<1>(CgZnorm<S>{t}, d_active));
+      WCL_CHECK(map(CgP<S>{t, p, d_sc}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active));  // q = M p
+      WCL_CHECK(reduce<1>(CgAlpha<S>{v}, d_active));
+      WCL_CHECK(reduce<1>(CgUpdate<S, X>{xs, p, r, v, d_sc}, d_active));
+    }
+    return WCL_OK;
+  }
+
+  wcl_status chunk(int n) {
+    if (gexec) {
+      WCL_CUDA(cudaGraphLaunch(gexec, c0->stream));
+      c0->kernel_launches += g_launches;
+      c0->dslash_launches += g_dslash;
+      return WCL_OK;
+    }
+    for (int k = 0; k < n; k++) WCL_CHECK(iteration());
+    return WCL_OK;
+  }
+
+  wcl_status capture(int n) {
+    cudaGraph_t g = nullptr;
+    WCL_CUDA(cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal));
+    c0->capturing = true;
+    c0->capture_launches = c0->capture_dslash = 0;
+    g_ev0 = c0->ev_used;
+    wcl_status s = WCL_OK;
+    for (int k = 0; k < n && s == WCL_OK; k++) s = iteration();
+    c0->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(c0->stream, &g);
+    if (s != WCL_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    g_ev1 = c0->ev_used;
+    g_launches = c0->capture_launches;
+    g_dslash = c0->capture_dslash;
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return WCL_OK;
+  }
+
+  // ---- reliable update on the slices flagged in h_upd ------------------------
+  wcl_status reliable_update(bool restart) {
+    WCL_CHECK(map(AddInto64<X>{x, xs}, d_upd));
+    WCL_CHECK(apply_mhat(ctxs, F64, nrhs, r64, x, tmp64, false, d_upd));
+    WCL_CHECK(reduce<3>(ResidualReplace<S>{r64, bhat, r, rhat, (!cg && !restart) ? 1 : 0}, d_upd));
+    if (restart) WCL_CHECK(restart_krylov(d_upd));
+    return WCL_OK;
+  }
+
+  // fresh Krylov space from the current residual on the flagged slices
+  wcl_status restart_krylov(const int* mask) {
+    if (!cg) {
+      WCL_CHECK(convert(ctxs, S, S, nrhs, rhat, r, mask));
+      WCL_CHECK(map(ZeroPair<S>{p, v}, mask));
+      WCL_CHECK(reduce<3>(BicgRho<S>{rhat, r, RHO_INIT}, mask));
+    } else {
+      WCL_CHECK(map(ZeroPair<S>{p, v}, mask));
+      WCL_CHECK(map(ResetCg{d_sc}, mask));
+    }
+    return WCL_OK;
+  }
+
+  void profile_sync() {
+    if (!c0->profiling) return;
+    if (gexec) {
+      profile_accum_range(c0, g_ev0, g_ev1);
+      profile_flush(c0, g_ev1);
+    } else {
+      profile_flush(c0, 0);
+    }
+  }
+
+  // ---- the whole solve -------------------------------------------------------
+  wcl_status run(const SolveIO& io, wcl_solve_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    c0 = ctxs[0];
+    nslot = (int)ctxs.size() * nrhs;
+    cg = prm.solver == WCL_CGNR;
+    blk = c0->blas_block;
+    bb = make_batch(ctxs, nrhs, blk, RED_MAXCH);
+    WCL_CHECK(alloc());
+    stop2.assign(nslot, 0);
+    r2max.assign(nslot, 0);
+    iters.assign(nslot, 0);
+    updates.assign(nslot, 0);
+    restarts.assign(nslot, 0);
+    status.assign(nslot, WCL_OK);
+    WCL_CUDA(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * nslot, c0->stream));
+    for (int s = 0; s < nslot; s++) h_active[s] = 1, h_upd[s] = 0;
+    WCL_CHECK(push_masks());
+    WCL_CUDA(cudaMemsetAsync(c0->d_flags, 0, sizeof(int), c0->stream));
+
+    // import b (both parities) into FP64 internal fields
+    for (size_t l = 0; l < ctxs.size(); l++) {
+      const LatticeDevice& L = ctxs[l]->lat;
+      const long rs = 2 * L.vh * 12;
+      WCL_CUDA(import_fermion(L, io.d_b[l], rs, 0, nrhs, b_e.ptr[l], c0->d_flags, c0->stream));
+      WCL_CUDA(import_fermion(L, io.d_b[l], rs, L.vh * 12, nrhs, b_o.ptr[l], c0->d_flags, c0->stream));
+      count_launch(c0);
+      count_launch(c0);
+    }
+    // b_hat = b_e + kappa D_eo A_oo^-1 b_o
+    WCL_CHECK(clover_apply(ctxs, F64, nrhs, tmp64, b_o, 1, CL_AINV, nullptr));
+    WCL_CHECK(dslash(ctxs, F64, nrhs, bhat, tmp64, &b_e, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
+    WCL_CHECK(reduce<1>(Norm2<F64>{b_e, b_e, 2, 0, 0}, nullptr));
+    WCL_CHECK(reduce<1>(Norm2<F64>{b_o, b_o, 2, 1, 0}, nullptr));
+    WCL_CHECK(reduce<1>(Norm2<F64>{bhat, bhat, 1, 0, 0}, nullptr));
+    WCL_CHECK(zero(x, F64));
+    WCL_CHECK(zero(xs, X));
+    WCL_CHECK(zero(p, S));
+    WCL_CHECK(zero(v, S));
+    WCL_CHECK(convert(ctxs, F64, F64, nrhs, r64, bhat, nullptr));
+    WCL_CHECK(convert(ctxs, S, F64, nrhs, r, bhat, nullptr));
+    WCL_CHECK(convert(ctxs, S, S, nrhs, rhat, r, nullptr));
+    if (!cg) WCL_CHECK(reduce<3>(BicgRho<S>{rhat, r, RHO_INIT}, nullptr));
+    WCL_CHECK(sync_scalars());
+    int hflag = 0;
+    WCL_CUDA(cudaMemcpy(&hflag, c0->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hflag & 1) {
+      set_error("non-finite entry in the right-hand side");
+      return WCL_ERR_NONFINITE;
+    }
+    const double tol2 = prm.tol * prm.tol;
+    const double safety = 0.81;  // aim 10% below the target on the Schur residual
+    int nactive = 0;
+    for (int s = 0; s < nslot; s++) {
+      const double b2 = h_sc[s].aux[2];
+      stop2[s] = tol2 * b2 * safety;
+      r2max[s] = h_sc[s].aux[1];
+      if (!(b2 > 0.0)) {
+        h_active[s] = 0;  // zero source: x = 0 exactly
+      } else {
+        nactive++;
+      }
+    }
+    WCL_CHECK(push_masks());
+
+    const int ce = std::max(1, prm.check_every);
+    const double d2 = prm.delta_reliable * prm.delta_reliable;
+    bool graphs = prm.use_graphs != 0;
+    while (nactive > 0) {
+      if (graphs && !gexec) {
+        wcl_status s = capture(ce);
+        if (s != WCL_OK) {
+          graphs = false;  // fall back to direct launches of the same kernels
+          set_error("");
+        }
+      }
+      WCL_CHECK(chunk(ce));
+      WCL_CHECK(sync_scalars());
+      profile_sync();
+      bool any = false;
+      for (int s = 0; s < nslot; s++) {
+        h_upd[s] = 0;
+        if (!h_active[s]) continue;
+        iters[s] += ce;
+        const double r2 = h_sc[s].r2;
+        r2max[s] = std::max(r2max[s], r2);
+        const bool brk = (h_sc[s].flags & 1) || !(r2 == r2);
+        if (r2 <= stop2[s] || r2 < d2 * r2max[s] || brk || iters[s] >= prm.maxiter) {
+          h_upd[s] = 1;
+          any = true;
+        }
+      }
+      if (!any) continue;
+      WCL_CHECK(push_masks());
+      WCL_CHECK(reliable_update(prm.restart_on_update != 0));
+      WCL_CHECK(sync_scalars());
+      profile_sync();
+      bool restart_any = false;
+      for (int s = 0; s < nslot; s++) {
+        if (!h_upd[s]) continue;
+        updates[s]++;
+        const double tr2 = h_sc[s].aux[0];
+        const bool brk = (h_sc[s].flags & 1) != 0;
+        r2max[s] = tr2;
+        if (!(tr2 == tr2) || std::isinf(tr2)) {
+          status[s] = WCL_ERR_NONFINITE;
+          h_active[s] = 0;
+          nactive--;
+        } else if (tr2 <= stop2[s]) {
+          h_active[s] = 0;
+          nactive--;
+        } else if (iters[s] >= prm.maxiter) {
+          status[s] = WCL_ERR_NOT_CONVERGED;
+          h_active[s] = 0;
+          nactive--;
+        } else if (brk) {
+          if (++restarts[s] > 3) {
+            status[s] = WCL_ERR_BREAKDOWN;
+            h_active[s] = 0;
+            nactive--;
+          } else {
+            restart_any = true;
+          }
+        }
+        if (!(brk && h_active[s])) h_upd[s] = 0;  // keep the mask only for restarts
+      }
+      if (restart_any) {
+        for (int s = 0; s < nslot; s++) h_sc[s].flags = 0;
+        WCL_CHECK(push_masks());
+        WCL_CUDA(cudaMemcpyAsync(d_sc, h_sc, sizeof(Scalars) * nslot, cudaMemcpyHostToDevice, c0->stream));
+        WCL_CHECK(restart_krylov(d_upd));
+      }
+      for (int s = 0; s < nslot; s++) h_upd[s] = 0;
+      WCL_CHECK(push_masks());
+    }
+    if (gexec) {
+      cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+    }
+
+    // finish: fold in x_s, reconstruct x_o, true residual on the whole lattice
+    WCL_CHECK(map(AddInto64<X>{x, xs}, nullptr));
+    WCL_CHECK(dslash(ctxs, F64, nrhs, x_o, x, &b_o, 1, false, CL_AINV, CL_NONE, C_KAPPA, C_ONE, nullptr));
+    WCL_CHECK(dslash(ctxs, F64, nrhs, r64, x_o, &x, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
+    WCL_CHECK(dslash(ctxs, F64, nrhs, tmp64, x, &x_o, 1, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
+    WCL_CHECK(reduce<1>(Norm2<F64>{b_e, r64, 3, 0, 1}, nullptr));
+    WCL_CHECK(reduce<1>(Norm2<F64>{b_o, tmp64, 3, 1, 1}, nullptr));
+    for (size_t l = 0; l < ctxs.size(); l++) {
+      const LatticeDevice& L = ctxs[l]->lat;
+      const long rs = 2 * L.vh * 12;
+      WCL_CUDA(export_fermion(L, x.ptr[l], nrhs, io.d_x[l], rs, 0, c0->stream));
+      WCL_CUDA(export_fermion(L, x_o.ptr[l], nrhs, io.d_x[l], rs, L.vh * 12, c0->stream));
+      count_launch(c0);
+      count_launch(c0);
+    }
+    WCL_CHECK(sync_scalars());
+    profile_flush(c0, 0);
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    wcl_status worst = WCL_OK;
+    for (int s = 0; s < nslot; s++) {
+      const double b2 = h_sc[s].aux[2];
+      const double tr = b2 > 0 ? std::sqrt(h_sc[s].aux[3] / b2) : 0.0;
+      info[s].iters = iters[s];
+      info[s].true_residual = tr;
+      info[s].reliable_updates = updates[s];
+      if (status[s] == WCL_OK && !(tr <= prm.tol)) status[s] = (tr == tr) ? WCL_ERR_NOT_CONVERGED : WCL_ERR_NONFINITE;
+      info[s].status = status[s];
+      info[s].seconds = secs;
+      if (worst == WCL_OK && status[s] != WCL_OK) worst = (wcl_status)status[s];
+    }
+    if (worst != WCL_OK) set_error("right-hand side did not reach the tolerance: %s", worst == WCL_ERR_NOT_CONVERGED ? "maxiter" : "breakdown / non-finite");
+    return worst;
+  }
+};
+
+template <int S>
+wcl_status krylov_solve(const std::vector<wcl_ctx*>& ctxs, int nrhs, const wcl_solve_params& prm, const SolveIO& io,
+                        wcl_solve_info* info) {
+  KrylovSolver<S> ks;
+  ks.ctxs = ctxs;
+  ks.nrhs = nrhs;
+  ks.prm = prm;
+  wcl_status st = ks.run(io, info);
+  if (ks.gexec) cudaGraphExecDestroy(ks.gexec);
+  return st;
+}
+
+}  // namespace wcl

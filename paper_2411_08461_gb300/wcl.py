@@ -1,0 +1,232 @@
+"""ctypes binding of libwcl: argument marshalling only, same names as include/wcl.h.
+
+All arithmetic happens in the CUDA library.  Tensors are torch CUDA tensors
+(PyTorch supplies device memory and streams); their ``data_ptr()`` is passed
+straight through.  If the library has not been built, every call raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwcl.so")
+
+WCL_OK = 0
+STATUS_NAMES = {
+    0: "WCL_OK", 1: "WCL_ERR_INVALID_ARG", 2: "WCL_ERR_CUDA", 3: "WCL_ERR_OOM", 4: "WCL_ERR_NOT_CONVERGED",
+    5: "WCL_ERR_BREAKDOWN", 6: "WCL_ERR_NONFINITE", 7: "WCL_ERR_RECONSTRUCT", 8: "WCL_ERR_TIMEOUT",
+    9: "WCL_ERR_NO_GAUGE", 10: "WCL_ERR_NO_PRECOND",
+}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2}
+
+
+class wcl_solve_params(ctypes.Structure):
+    _fields_ = [
+        ("solver", ctypes.c_int), ("outer", ctypes.c_int), ("sloppy", ctypes.c_int), ("tol", ctypes.c_double),
+        ("maxiter", ctypes.c_int), ("delta_reliable", ctypes.c_double), ("restart_on_update", ctypes.c_int),
+        ("gcr_nkrylov", ctypes.c_int), ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int),
+    ]
+
+
+class wcl_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int), ("true_residual", ctypes.c_double), ("reliable_updates", ctypes.c_int),
+        ("status", ctypes.c_int), ("seconds", ctypes.c_double),
+    ]
+
+
+class wcl_stats(ctypes.Structure):
+    _fields_ = [
+        ("kernel_launches", ctypes.c_longlong), ("dslash_launches", ctypes.c_longlong), ("dslash_ms", ctypes.c_double),
+        ("dslash_timed", ctypes.c_longlong), ("dslash_bytes", ctypes.c_double), ("dslash_flops", ctypes.c_double),
+    ]
+
+
+class WclError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+#: every symbol include/wcl.h declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "wcl_default_params": (None, [ctypes.POINTER(wcl_solve_params)]),
+    "wcl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "wcl_last_error": (ctypes.c_char_p, []),
+    "wcl_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, _P]),
+    "wcl_load_gauge": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double]),
+    "wcl_apply_D": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
+    "wcl_apply_Mpc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "wcl_invert": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_solve_params),
+                                  ctypes.POINTER(wcl_solve_info)]),
+    "wcl_invert_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                        ctypes.c_int, ctypes.POINTER(wcl_solve_params),
+                                        ctypes.POINTER(wcl_solve_info)]),
+    "wcl_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wcl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(wcl_stats), ctypes.c_int]),
+    "wcl_destroy": (ctypes.c_int, [_P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Open libwcl.so and declare every exported signature; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libwcl.so not built at {path}: run __graft_entry__.build() "
+                           "(there is no CPU fallback for the CUDA path)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != WCL_OK:
+        msg = load_library().wcl_last_error().decode(errors="replace")
+        raise WclError(status, where, msg)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (Sec. II.B: contiguous fields only)")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def wcl_default_params(**overrides) -> wcl_solve_params:
+    p = wcl_solve_params()
+    load_library().wcl_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k in ("outer", "sloppy") and isinstance(v, str):
+            v = PREC[v]
+        if k == "solver" and isinstance(v, str):
+            v = SOLVER[v]
+        setattr(p, k, v)
+    return p
+
+
+def wcl_status_string(status: int) -> str:
+    return load_library().wcl_status_string(status).decode()
+
+
+class Context:
+    """One lattice on one GPU (wcl_create ... wcl_destroy)."""
+
+    def __init__(self, dims: Sequence[int], t_boundary: int = -1, device: int = 0, stream=None):
+        import torch
+
+        lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        lx, ly, lz, lt = self.dims
+        self.volume = lx * ly * lz * lt
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.dims)
+        _check(lib.wcl_create(ctypes.byref(handle), d, int(t_boundary), int(device), ctypes.c_void_p(stream.cuda_stream)),
+               "wcl_create")
+        self.handle = handle
+
+    # fields are complex128 in the QDP layout
+    @property
+    def fermion_numel(self) -> int:
+        return self.volume * 12
+
+    def wcl_load_gauge(self, gauge, kappa: float, csw: float):
+        import torch
+
+        _check(load_library().wcl_load_gauge(self.handle, _ptr(gauge, torch.complex128, self.volume * 36, "gauge"),
+                                             float(kappa), float(csw)), "wcl_load_gauge")
+
+    def wcl_apply_D(self, out, inp, prec: str = "f64", nrhs: int = 1):
+        import torch
+
+        n = self.fermion_numel * nrhs
+        _check(load_library().wcl_apply_D(self.handle, _ptr(out, torch.complex128, n, "out"),
+                                          _ptr(inp, torch.complex128, n, "in"), PREC[prec], nrhs), "wcl_apply_D")
+
+    def wcl_apply_Mpc(self, out_e, in_e, prec: str = "f64", nrhs: int = 1, dagger: bool = False):
+        import torch
+
+        n = self.fermion_numel // 2 * nrhs
+        _check(load_library().wcl_apply_Mpc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
+                                            _ptr(in_e, torch.complex128, n, "in_e"), PREC[prec], nrhs, int(dagger)),
+               "wcl_apply_Mpc")
+
+    def wcl_invert(self, x, b, nrhs: int = 1, params: wcl_solve_params | None = None, check: bool = True):
+        import torch
+
+        params = params or wcl_default_params()
+        info = (wcl_solve_info * nrhs)()
+        n = self.fermion_numel * nrhs
+        st = load_library().wcl_invert(self.handle, _ptr(x, torch.complex128, n, "x"), _ptr(b, torch.complex128, n, "b"),
+                                       nrhs, ctypes.byref(params), info)
+        if check:
+            _check(st, "wcl_invert")
+        return st, [_info_dict(i) for i in info]
+
+    def wcl_set_profiling(self, enable: bool = True):
+        _check(load_library().wcl_set_profiling(self.handle, int(enable)), "wcl_set_profiling")
+
+    def wcl_get_stats(self, reset: bool = False) -> dict:
+        s = wcl_stats()
+        _check(load_library().wcl_get_stats(self.handle, ctypes.byref(s), int(reset)), "wcl_get_stats")
+        return {k: getattr(s, k) for k, _ in wcl_stats._fields_}
+
+    def wcl_destroy(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().wcl_destroy(self.handle)
+            self.handle = None
+
+    close = wcl_destroy
+
+    def __del__(self):
+        try:
+            self.wcl_destroy()
+        except Exception:
+            pass
+
+
+def _info_dict(i: wcl_solve_info) -> dict:
+    return {"iters": i.iters, "true_residual": i.true_residual, "reliable_updates": i.reliable_updates,
+            "status": i.status, "seconds": i.seconds}
+
+
+def wcl_invert_batch(ctxs: Sequence[Context], xs, bs, nrhs: int, params: wcl_solve_params | None = None,
+                     check: bool = True):
+    """Several lattices, one launch per solver step (wcl_invert_batch)."""
+    import torch
+
+    params = params or wcl_default_params()
+    n = len(ctxs)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, c.fermion_numel * nrhs, "x").value for c, x in zip(ctxs, xs)])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b, torch.complex128, c.fermion_numel * nrhs, "b").value for c, b in zip(ctxs, bs)])
+    info = (wcl_solve_info * (n * nrhs))()
+    st = load_library().wcl_invert_batch(hs, n, xp, bp, nrhs, ctypes.byref(params), info)
+    if check:
+        _check(st, "wcl_invert_batch")
+    return st, [_info_dict(i) for i in info]

@@ -1,0 +1,144 @@
+"""GPU solves: the true residual recomputed by the FP64 oracle must meet the tolerance."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dirac
+from oracle import lattice as L
+
+from _gpu import built, cuda, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    return built()
+
+
+def _oracle_true_residual(op, x_qdp, b_qdp):
+    return op.true_residual(L.from_qdp(x_qdp, op.dims), L.from_qdp(b_qdp, op.dims))
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_plain_fp64_point_source(pkg, solver, graphs):
+    """4^4, eps 0.2, kappa 0.12, c_sw 1, point source (site 0, spin 0, colour 0), tol 1e-12."""
+    dims = (4, 4, 4, 4)
+    gauge = W.gauge_links(dims, 0.2, 0)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.12, 1.0)
+    b = W.point_source(dims, 0, 0)
+    x = cuda(np.zeros_like(b))
+    prm = pkg.wcl_default_params(solver=solver, sloppy="f64", tol=1e-12, use_graphs=graphs)
+    _, info = ctx.wcl_invert(x, cuda(b), 1, prm)
+    op = dirac.from_qdp_problem(gauge, dims, 0.12, 1.0)
+    tr = _oracle_true_residual(op, host(x), b)
+    assert tr <= 1e-12
+    assert abs(tr - info[0]["true_residual"]) <= 1e-3 * tr + 1e-15
+    # and the solution itself agrees with the oracle's own solve
+    from oracle import solvers
+    xo, _ = solvers.solve_even_odd(op, L.from_qdp(b, dims), tol=1e-13)
+    assert np.linalg.norm(L.from_qdp(host(x), dims) - xo) <= 1e-10 * np.linalg.norm(xo)
+    ctx.close()
+
+
+@pytest.mark.parametrize("sloppy", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
+def test_mixed_precision_reaches_1e10(pkg, sloppy, solver):
+    dims = (8, 8, 8, 16)
+    gauge = W.gauge_links(dims, 0.3, 0)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    b = W.gaussian_fermion(dims, 1)
+    x = cuda(np.zeros_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 1, pkg.wcl_default_params(solver=solver, sloppy=sloppy, tol=1e-10))
+    op = dirac.from_qdp_problem(gauge, dims, 0.1235, 1.0)
+    tr = _oracle_true_residual(op, host(x), b)
+    assert tr <= 1e-10, (tr, info)
+    assert info[0]["reliable_updates"] >= 1
+    ctx.close()
+
+
+def test_twelve_spin_colour_sources(pkg):
+    dims = (4, 4, 4, 8)
+    gauge = W.gauge_links(dims, 0.3, 2)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    b = np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])
+    x = cuda(np.zeros_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 12, pkg.wcl_default_params(sloppy="f16", tol=1e-10))
+    op = dirac.from_qdp_problem(gauge, dims, 0.1235, 1.0)
+    xh = host(x)
+    for k in range(12):
+        assert _oracle_true_residual(op, xh[k], b[k]) <= 1e-10
+        assert info[k]["status"] == 0
+    ctx.close()
+
+
+def test_batch_of_uneven_lattices(pkg):
+    shapes = [(4, 4, 4, 8), (6, 6, 6, 12), (8, 4, 4, 8)]
+    ctxs, ops, bs, xs = [], [], [], []
+    for k, dims in enumerate(shapes):
+        g = W.gauge_links(dims, 0.3, 10 + k)
+        c = pkg.Context(dims)
+        c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
+        ctxs.append(c)
+        ops.append(dirac.from_qdp_problem(g, dims, 0.1235, 1.0))
+        b = W.z2_fermion(dims, 20 + k, nrhs=3)
+        bs.append(b)
+        xs.append(cuda(np.zeros_like(b)))
+    _, info = pkg.wcl_invert_batch(ctxs, xs, [cuda(b) for b in bs], 3, pkg.wcl_default_params(sloppy="f32", tol=1e-10))
+    for k in range(len(shapes)):
+        xh = host(xs[k])
+        for r in range(3):
+            assert _oracle_true_residual(ops[k], xh[r], bs[k][r]) <= 1e-10
+    for c in ctxs:
+        c.close()
+
+
+def test_zero_source_gives_zero(pkg):
+    dims = (4, 4, 4, 4)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(W.gauge_links(dims, 0.2, 0)), 0.12, 1.0)
+    b = np.zeros((2, 4, 4, 4, 2, 4, 3), dtype=np.complex128)
+    x = cuda(np.ones_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 1, pkg.wcl_default_params())
+    assert np.all(host(x) == 0) and info[0]["status"] == 0
+    ctx.close()
+
+
+# --- failures surface as status codes (all made on the host side) ----------------
+
+def test_errors(pkg):
+    from paper_2411_08461_gb300.wcl import WclError
+
+    dims = (4, 4, 4, 4)
+    with pytest.raises(WclError) as e:
+        pkg.Context((3, 4, 4, 4))
+    assert e.value.status == 1
+    ctx = pkg.Context(dims)
+    b = cuda(W.point_source(dims, 0, 0))
+    x = cuda(np.zeros((2, 4, 4, 4, 2, 4, 3), dtype=np.complex128))
+    st, _ = ctx.wcl_invert(x, b, 1, check=False)
+    assert st == 9  # no gauge
+    bad = W.gauge_links(dims, 0.2, 0) * 1.001  # not unitary
+    with pytest.raises(WclError) as e:
+        ctx.wcl_load_gauge(cuda(bad), 0.12, 1.0)
+    assert e.value.status == 7
+    nan = W.gauge_links(dims, 0.2, 0)
+    nan[0, 0, 0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(WclError) as e:
+        ctx.wcl_load_gauge(cuda(nan), 0.12, 1.0)
+    assert e.value.status == 6
+    ctx.wcl_load_gauge(cuda(W.gauge_links(dims, 0.2, 0)), 0.12, 1.0)
+    st, info = ctx.wcl_invert(x, b, 1, pkg.wcl_default_params(maxiter=4, check_every=2), check=False)
+    assert st == 4 and info[0]["status"] == 4 and info[0]["iters"] >= 4
+    assert 0 < info[0]["true_residual"] < 1
+    bn = W.point_source(dims, 0, 0)
+    bn[0, 0, 0, 0, 1, 0, 0] = np.inf
+    st, _ = ctx.wcl_invert(x, cuda(bn), 1, check=False)
+    assert st == 6
+    st, _ = ctx.wcl_invert(x, b, 1, pkg.wcl_default_params(solver="fgcr_learned"), check=False)
+    assert st == 10
+    ctx.close()

@@ -163,3 +163,15 @@ def test_dense_matrix_matches(dims, t_boundary):
     full = np.zeros_like(psi).ravel()
     full[ie] = xe_exact
     np.testing.assert_allclose(op.reconstruct(full.reshape(psi.shape), b).ravel(), xs, atol=1e-11)
+
+
+def test_site_by_site_evaluation_matches_whole_lattice():
+    dims = (4, 2, 6, 4)
+    gq = W.gauge_links(dims, 0.6, 17)
+    psi_q = W.gaussian_fermion(dims, 18)
+    op = dirac.from_qdp_problem(gq, dims, 0.127, 1.3)
+    full = op.M(L.from_qdp(psi_q, dims))
+    sites = [(0, 0, 0, 0), (3, 1, 5, 3), (1, 0, 2, 0), (2, 1, 0, 3)]
+    vals = dirac.M_at_sites(gq, psi_q, dims, 0.127, 1.3, sites)
+    for (x, y, z, t), v in zip(sites, vals):
+        np.testing.assert_allclose(v, full[t, z, y, x], atol=1e-13)
