@@ -26,7 +26,10 @@ wcl_status enter(wcl_ctx* c) {
 }
 
 wcl_status leave(wcl_ctx* c, wcl_status s) {
-  cudaError_t e = cudaStreamSynchronize(c->stream);
+  // later work on the caller's stream is ordered after this call's work
+  cudaError_t e = cudaEventRecord(c->ev_out, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->user_stream, c->ev_out, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess && s == WCL_OK) return cuda_fail(e, "cudaStreamSynchronize");
   return s;
 }
