@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update threshold")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -215,7 +216,8 @@ def run_ours(args, rank, world, local):
     del gauge
     b = torch.from_numpy(src).to(dev)
     x = torch.zeros_like(b)
-    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=TOL, check_every=8)
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=TOL, check_every=8,
+                                 delta_reliable=args.delta)
 
     infos = None
     for _ in range(args.warmup):
@@ -281,7 +283,7 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{args.sloppy} storage / f32 arithmetic / f64 residual", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "nrhs": 12, "solver": "bicgstab even-odd",
-                   "sloppy": args.sloppy, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "sloppy": args.sloppy, "delta_reliable": args.delta, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set >> L2 (no flush needed)"},
         "solve": {"seconds": ms / 1e3, "iters_per_rhs": iters, "worst_true_residual": worst,
                   "reliable_updates": statistics.mean(i["reliable_updates"] for i in infos)},

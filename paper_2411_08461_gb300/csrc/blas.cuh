@@ -333,15 +333,20 @@ struct BicgUpdate {  // x += alpha p + omega s; r = s - omega t; then rho' and |
   __device__ void finalize(Scalars& c, const double* t) const { bicg_rho_finalize(c, make_double2(t[0], t[1]), t[2], RHO_NORMAL); }
 };
 
-// reliable update: r64 = bhat - y (y = M_hat x64 already in r64), rS = r64,
-// aux[0] = ||r64||^2; BiCGStab also recomputes rho against rhat (REPLACE)
+// reliable update: r64 = b_e - y with y = A_ee x_e - kappa D_eo x_o already in
+// r64 (x_o the reconstructed odd solution), so r64 is the FP64 Schur residual
+// b_hat - M_hat x_e; rS = r64.  ro holds the odd residual b_o - (A_oo x_o - kappa D_oe x_e).
+// aux[0] = ||r_e||^2, aux[3] = ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true residual).
+// BiCGStab also recomputes rho against rhat (REPLACE).
 template <int S>
 struct ResidualReplace {
-  FieldRef r64, bhat, rS, rhat;
+  FieldRef r64, bhat, rS, rhat, ro;
   int bicg;  // 1: BiCGStab rho REPLACE finalize; 0: CG (only the norm)
   __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
     using R = typename Traits<S>::R;
     cpx<double> y[12], b[12];
+    WCL_LD(F64, true, b, ro);
+    acc[3] += norm_site(b);
     WCL_LD(F64, false, y, r64);
     WCL_LD(F64, true, b, bhat);
     cpx<R> rs[12];
@@ -367,6 +372,7 @@ struct ResidualReplace {
   }
   __device__ void finalize(Scalars& c, const double* t) const {
     c.aux[0] = t[0];
+    c.aux[3] = t[0] + t[3];
     if (bicg) {
       bicg_rho_finalize(c, make_double2(t[1], t[2]), t[0], RHO_REPLACE);
     } else {

@@ -86,7 +86,7 @@ Batch make_batch(const std::vector<wcl_ctx*>& ctxs, int nrhs, int block, int cap
 
 static void spinor_site_bytes(int prec, double& sp, double& link, double& clov) {
   switch (prec) {
-    case F64: sp = 192; link = 96; clov = 576; break;
+    case F64: sp = 192; link = 144; clov = 576; break;
     case F32: sp = 96; link = 48; clov = 288; break;
     default: sp = 52; link = 24; clov = 148; break;
   }
@@ -107,6 +107,12 @@ static wcl_ctx::Timed* prof_begin(wcl_ctx* c) {
 wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                   const FieldRef* x, int out_parity, bool dagger, CloverSel post, CloverSel pre, Coef alpha,
                   Coef beta, const int* active) {
+  return dslash_ex(ctxs, prec, nrhs, out, in, x, nullptr, out_parity, dagger, post, pre, alpha, beta, active);
+}
+
+wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
+                     const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
+                     CloverSel pre, Coef alpha, Coef beta, const int* active) {
   wcl_ctx* c0 = ctxs[0];
   const int block = c0->dslash_block[prec];
   DslashArgs a;
@@ -115,6 +121,7 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
   a.out = out;
   a.in = in;
   if (x) a.x = *x;
+  if (out2) a.out2 = *out2;
   a.out_parity = out_parity;
   a.active = active;
   double sites = 0;
@@ -139,6 +146,7 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
   if (post) mode |= MODE_POST;
   if (x) mode |= MODE_XPAY;
   if (x && pre) mode |= MODE_PRE;
+  if (out2) mode |= MODE_RECON;
   wcl_ctx::Timed* t = prof_begin(c0);
   cudaError_t e;
   switch (prec) {
@@ -153,13 +161,13 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
     cudaEventRecord(t->b, c0->stream);
     double sp, lk, cl;
     spinor_site_bytes(prec, sp, lk, cl);
-    double per = 8 * lk + 2 * sp + (post ? cl : 0) + (x ? sp : 0) + (x && pre ? cl : 0);
+    double per = 8 * lk + 2 * sp + (post ? cl : 0) + (x ? sp : 0) + (x && pre ? cl : 0) + (out2 ? sp : 0);
     // links and clover are shared by the right-hand sides of a site
     double per_site_shared = 8 * lk + (post ? cl : 0) + (x && pre ? cl : 0);
     double per_rhs = per - per_site_shared;
     double base_sites = sites / nrhs;
     t->bytes = base_sites * per_site_shared + sites * per_rhs;
-    t->flops = sites * (1320.0 + ((post || (x && pre)) ? 504.0 : 0.0) + (x ? 48.0 : 0.0));
+    t->flops = sites * (1320.0 + (post ? 504.0 : 0.0) + ((x && pre) ? 504.0 : 0.0) + (x ? 48.0 : 0.0));
   }
   return WCL_OK;
 }

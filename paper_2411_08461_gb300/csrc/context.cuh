@@ -98,6 +98,11 @@ enum CloverSel { CL_NONE = 0, CL_A = 1, CL_AINV = 2 };
 wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                   const FieldRef* x, int out_parity, bool dagger, CloverSel post, CloverSel pre, Coef alpha,
                   Coef beta, const int* active);
+// as dslash, with an optional second output: when out2 is given (post = A^-1,
+// pre = A, x given) out = A^-1 t and out2 = t - A out for t = alpha D in + beta x
+wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
+                     const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
+                     CloverSel pre, Coef alpha, Coef beta, const int* active);
 // out = C x on parity `parity`
 wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out,
                         const FieldRef& x, int parity, CloverSel which, const int* active);

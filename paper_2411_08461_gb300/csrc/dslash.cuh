@@ -21,11 +21,15 @@
 
 namespace wcl {
 
-enum DslashMode { MODE_POST = 1, MODE_XPAY = 2, MODE_PRE = 4 };
+// MODE_RECON (with POST, XPAY and PRE): t = alpha D in + beta x, out = C_post t,
+// out2 = t - C_pre out.  With C_post = A^-1, C_pre = A this reconstructs the odd
+// solution x_o = A_oo^-1 (b_o + kappa D_oe x_e) and its residual b_o - (A x_o - kappa D x_e)
+// in one pass over the links.
+enum DslashMode { MODE_POST = 1, MODE_XPAY = 2, MODE_PRE = 4, MODE_RECON = 8 };
 
 struct DslashArgs {
   Batch b;
-  FieldRef out, in, x;
+  FieldRef out, in, x, out2;
   const void* gauge[MAXLAT][2];  // per parity: [mu][chunk][stride]
   const void* cpost[MAXLAT];
   const float* cpost_norm[MAXLAT];
@@ -181,6 +185,20 @@ __global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ Dsl
 #pragma unroll
   for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
 
+  if (MODE & MODE_RECON) {
+    cpx<R> xv[12], y2[12], ay[12];
+    SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, s.rhs, stride), rhs_norm(a.x, s.l, s.rhs, stride), stride, i);
+    const R beta = R(a.beta[s.l]);
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
+    CloverIO<P>::apply(y2, acc, a.cpost[s.l], a.cpost_norm[s.l], stride, i);
+    CloverIO<P>::apply(ay, y2, a.cpre[s.l], a.cpre_norm[s.l], stride, i);
+#pragma unroll
+    for (int k = 0; k < 12; k++) ay[k] = acc[k] - ay[k];
+    SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, s.rhs, stride), rhs_norm(a.out, s.l, s.rhs, stride), stride, i);
+    SpinorIO<P>::store(ay, rhs_ptr_w<P>(a.out2, s.l, s.rhs, stride), rhs_norm(a.out2, s.l, s.rhs, stride), stride, i);
+    return;
+  }
   if (MODE & MODE_XPAY) {
     cpx<R> xv[12];
     SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, s.rhs, stride), rhs_norm(a.x, s.l, s.rhs, stride), stride, i);
@@ -237,13 +255,15 @@ cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
   template <>                                                                                       \
   cudaError_t launch_dslash<P>(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st) { \
     dim3 grid(a.b.total_blocks), blk(block);                                                        \
-    switch (mode | (dagger ? 8 : 0)) {                                                              \
+    switch (mode | (dagger ? 16 : 0)) {                                                              \
       case MODE_POST: dslash_kernel<P, false, MODE_POST><<<grid, blk, 0, st>>>(a); break;            \
-      case MODE_POST | 8: dslash_kernel<P, true, MODE_POST><<<grid, blk, 0, st>>>(a); break;        \
+      case MODE_POST | 16: dslash_kernel<P, true, MODE_POST><<<grid, blk, 0, st>>>(a); break;        \
       case MODE_XPAY | MODE_PRE: dslash_kernel<P, false, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
-      case MODE_XPAY | MODE_PRE | 8: dslash_kernel<P, true, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
+      case MODE_XPAY | MODE_PRE | 16: dslash_kernel<P, true, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
       case MODE_XPAY: dslash_kernel<P, false, MODE_XPAY><<<grid, blk, 0, st>>>(a); break;            \
       case MODE_XPAY | MODE_POST: dslash_kernel<P, false, MODE_XPAY | MODE_POST><<<grid, blk, 0, st>>>(a); break; \
+      case MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON:                                           \
+        dslash_kernel<P, false, MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON><<<grid, blk, 0, st>>>(a); break; \
       default: return cudaErrorInvalidValue;                                                        \
     }                                                                                               \
     return cudaGetLastError();                                                                      \

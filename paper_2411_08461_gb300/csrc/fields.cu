@@ -72,9 +72,9 @@ __global__ void gauge_import_kernel(const double2* __restrict__ qdp, QdpGeom q, 
     dev = fmax(dev, fmax(fabs(det.re - 1.0), fabs(det.im)));
     if (!(dev <= tol)) atomicOr(flags, 2);
     const long st = out.stride;
-    // F64: 6 double2 chunks
-    double2* d64 = static_cast<double2*>(out.g64[p]) + (long)mu * 6 * st;
-    for (int k = 0; k < 6; k++) d64[k * st + i] = make_double2(u[k / 3][k % 3].re, u[k / 3][k % 3].im);
+    // F64: all 9 entries as double2 chunks
+    double2* d64 = static_cast<double2*>(out.g64[p]) + (long)mu * 9 * st;
+    for (int k = 0; k < 9; k++) d64[k * st + i] = make_double2(u[k / 3][k % 3].re, u[k / 3][k % 3].im);
     // F32: 3 float4 chunks
     float4* d32 = static_cast<float4*>(out.g32[p]) + (long)mu * 3 * st;
     for (int k = 0; k < 3; k++) {

@@ -28,7 +28,7 @@ inline size_t spinor_field_bytes(int prec, long stride) {
 }
 inline size_t gauge_parity_bytes(int prec, long stride) {
   switch (prec) {
-    case F64: return (size_t)4 * 6 * 16 * stride;
+    case F64: return (size_t)4 * 9 * 16 * stride;
     case F32: return (size_t)4 * 3 * 16 * stride;
     default: return (size_t)4 * 3 * 8 * stride;
   }

@@ -12,9 +12,11 @@
 //     RHS r of a field starts at base + r * (nchunk * stride) chunks
 //     (norms at norm + r*stride).
 //
-//   links, per parity p: [mu][chunk][stride], 12 reals = rows 0 and 1 of U_mu;
-//     row 2 is rebuilt as conj(row0 x row1) (exact for SU(3))
-//     F64 : 6 double2, F32 : 3 float4, F16/BF16 : 3 uint2 (4 reals each, |U_ij| <= 1)
+//   links, per parity p: [mu][chunk][stride]
+//     F64 : all 18 reals, 9 double2 (FP64 arithmetic is the scarce resource on
+//           GB300, so the FP64 operator skips the row-2 reconstruction)
+//     F32 : 12 reals = rows 0 and 1, 3 float4; row 2 rebuilt as conj(row0 x row1)
+//     F16/BF16 : the same 12 reals, 3 uint2 (4 reals each, |U_ij| <= 1)
 //
 //   clover, per parity: two Hermitian 6x6 chiral blocks (spins {0,1} and {2,3},
 //     index 3*spin_in_block + colour), each packed as 6 real diagonal entries
@@ -85,7 +87,7 @@ template <>
 struct Traits<F64> {
   using R = double;  // compute type
   static constexpr int SP_CHUNK = 12, SP_CHUNK_BYTES = 16;
-  static constexpr int LK_CHUNK = 6, LK_CHUNK_BYTES = 16;
+  static constexpr int LK_CHUNK = 9, LK_CHUNK_BYTES = 16;
   static constexpr int CL_CHUNK = 36, CL_CHUNK_BYTES = 16;
   static constexpr bool HAS_NORM = false;
 };
@@ -263,13 +265,12 @@ template <>
 struct LinkIO<F64> {
   using R = double;
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
-    const double2* p = static_cast<const double2*>(base) + (long)mu * 6 * stride;
+    const double2* p = static_cast<const double2*>(base) + (long)mu * 9 * stride;
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
+    for (int k = 0; k < 9; k++) {
       double2 d = ldg(p + k * stride + i);
       u[k / 3][k % 3] = {d.x, d.y};
     }
-    reconstruct_row2(u);
   }
 };
 template <>
