@@ -169,6 +169,34 @@ wcl_status wcl_set_profiling(wcl_ctx* ctx, int enable);
 /* Read (and with reset != 0, afterwards zero) the counters of ctx. */
 wcl_status wcl_get_stats(wcl_ctx* ctx, wcl_stats* out, int reset);
 
+/* Largest number of sites per parity (Vh rounded up to a multiple of 64) that
+ * wcl_apply_Mpc_noalloc accepts; e.g. 8^3x32, 16^3x8, 16x16x8x16. */
+#define WCL_NOALLOC_MAX_VH 16384
+
+/* d_out_e = M_hat d_in_e (dagger = 0) or M_hat^+ d_in_e (dagger = 1) in FP64 for
+ * one even half-field, exactly as wcl_apply_Mpc(ctx, d_out_e, d_in_e, WCL_F64, 1,
+ * dagger), but without allocating any memory in the call.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * let a library allocate device memory while they run -- for instance a program
+ * whose own pool allocator owns all device memory, or a time-critical loop that
+ * cannot accept cudaMalloc's implicit device synchronisation or its failure
+ * part-way through a run.  The context (links, clover) must be prepared
+ * beforehand with wcl_create / wcl_load_gauge.
+ *
+ * Scratch: the input copy, the odd-parity intermediate and the output live in
+ * one fixed device array of 3 x 192 x WCL_NOALLOC_MAX_VH bytes (9 MiB) that
+ * every GPU which loads the library holds until the process exits.  Lattices
+ * with more than WCL_NOALLOC_MAX_VH padded sites per parity are rejected with
+ * WCL_ERR_INVALID_ARG.  The first call on each device looks up the array's
+ * device address once (with that device current); make that first call before
+ * any stream capture.  Every call shares the array and leaves its contents
+ * behind (each call writes everything it reads, so nothing is cleared); calls
+ * whose GPU work overlaps -- from different streams, threads or contexts on the
+ * same device -- race on it and must be serialised by the caller.
+ *   d_in_e, d_out_e: device, [Lt][Lz][Ly][Lx/2][4][3] complex128, caller-owned. */
+wcl_status wcl_apply_Mpc_noalloc(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, int dagger);
+
 /* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */
 wcl_status wcl_destroy(wcl_ctx* ctx);
 

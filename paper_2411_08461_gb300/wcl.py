@@ -69,6 +69,7 @@ SIGNATURES = {
                                         ctypes.POINTER(wcl_solve_info)]),
     "wcl_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "wcl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(wcl_stats), ctypes.c_int]),
+    "wcl_apply_Mpc_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "wcl_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -175,6 +176,15 @@ class Context:
         _check(load_library().wcl_apply_Mpc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
                                             _ptr(in_e, torch.complex128, n, "in_e"), PREC[prec], nrhs, int(dagger)),
                "wcl_apply_Mpc")
+
+    def wcl_apply_Mpc_noalloc(self, out_e, in_e, dagger: bool = False):
+        """FP64 M_hat (or its adjoint) with the library's fixed scratch array: no allocation in the call."""
+        import torch
+
+        n = self.fermion_numel // 2
+        _check(load_library().wcl_apply_Mpc_noalloc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
+                                                    _ptr(in_e, torch.complex128, n, "in_e"), int(dagger)),
+               "wcl_apply_Mpc_noalloc")
 
     def wcl_invert(self, x, b, nrhs: int = 1, params: wcl_solve_params | None = None, check: bool = True):
         import torch
