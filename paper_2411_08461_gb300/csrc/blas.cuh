@@ -36,18 +36,14 @@ __global__ void __launch_bounds__(256) map_kernel(const __grid_constant__ Batch 
   for (long i = (long)s.chunk * blockDim.x + threadIdx.x; i < g.vh; i += (long)g.nchunk * blockDim.x) f(s, g, i);
 }
 
-template <int NR, typename F>
-__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Batch b, const __grid_constant__ F f,
-                                                     const int* __restrict__ active, double* __restrict__ partials,
-                                                     unsigned* __restrict__ counters, Scalars* __restrict__ sc) {
-  const Slice s = find_slice(b, blockIdx.x);
-  if (active && !active[s.slot]) return;
-  const LatGeom& g = b.lat[s.l];
-  double acc[NR];
-#pragma unroll
-  for (int k = 0; k < NR; k++) acc[k] = 0.0;
-  for (long i = (long)s.chunk * blockDim.x + threadIdx.x; i < g.vh; i += (long)g.nchunk * blockDim.x) f(s, g, i, acc);
-
+// Block-level reduction of NR doubles per thread for the slice s, one partial per
+// block, and the finalizer run once per slice by its last block (atomic ticket;
+// partials summed in a fixed order, so the result is deterministic).  Every
+// thread of the block must call it.  fin(Scalars&, const double* tot).
+template <int NR, typename Fin>
+__device__ __forceinline__ void slice_reduce(double acc[NR], const Slice& s, int nchunk, int maxch,
+                                             double* __restrict__ partials, unsigned* __restrict__ counters,
+                                             Scalars* __restrict__ sc, const Fin& fin) {
   __shared__ double sh[NR][32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -62,13 +58,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     for (int k = 0; k < NR; k++) {
       double v = lane < nw ? sh[k][lane] : 0.0;
       v = warp_sum(v);
-      if (lane == 0) partials[((size_t)s.slot * RED_MAXCH + s.chunk) * NR + k] = v;
+      if (lane == 0) partials[((size_t)s.slot * maxch + s.chunk) * NR + k] = v;
     }
   }
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&counters[s.slot], 1u);
-    last = (ticket == (unsigned)g.nchunk - 1u);
+    last = (ticket == (unsigned)nchunk - 1u);
   }
   __syncthreads();
   if (!last) return;
@@ -76,9 +72,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
   double tot[NR];
 #pragma unroll
   for (int k = 0; k < NR; k++) tot[k] = 0.0;
-  for (int c = threadIdx.x; c < g.nchunk; c += blockDim.x) {
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < NR; k++) tot[k] += __ldcg(partials + ((size_t)s.slot * RED_MAXCH + c) * NR + k);
+    for (int k = 0; k < NR; k++) tot[k] += __ldcg(partials + ((size_t)s.slot * maxch + c) * NR + k);
   }
   __syncthreads();
 #pragma unroll
@@ -94,10 +90,25 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
       tot[k] = warp_sum(v);
     }
     if (lane == 0) {
-      f.finalize(sc[s.slot], tot);
+      fin(sc[s.slot], tot);
       counters[s.slot] = 0u;
     }
   }
+}
+
+template <int NR, typename F>
+__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Batch b, const __grid_constant__ F f,
+                                                     const int* __restrict__ active, double* __restrict__ partials,
+                                                     unsigned* __restrict__ counters, Scalars* __restrict__ sc) {
+  const Slice s = find_slice(b, blockIdx.x);
+  if (active && !active[s.slot]) return;
+  const LatGeom& g = b.lat[s.l];
+  double acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; k++) acc[k] = 0.0;
+  for (long i = (long)s.chunk * blockDim.x + threadIdx.x; i < g.vh; i += (long)g.nchunk * blockDim.x) f(s, g, i, acc);
+  slice_reduce<NR>(acc, s, g.nchunk, RED_MAXCH, partials, counters, sc,
+                   [&](Scalars& c, const double* t) { f.finalize(c, t); });
 }
 
 // ---------------------------------------------------------------------------

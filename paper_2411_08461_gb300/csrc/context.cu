@@ -1,4 +1,5 @@
 // Context helpers: errors, workspace, batch geometry, operator launches, profiling.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -110,9 +111,16 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
   return dslash_ex(ctxs, prec, nrhs, out, in, x, nullptr, out_parity, dagger, post, pre, alpha, beta, active);
 }
 
+int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
+  const int block = ctxs[0]->dslash_block[prec];
+  long m = 1;
+  for (auto* c : ctxs) m = std::max(m, (c->lat.vh + block - 1) / block);
+  return (int)m;
+}
+
 wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                      const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
-                     CloverSel pre, Coef alpha, Coef beta, const int* active) {
+                     CloverSel pre, Coef alpha, Coef beta, const int* active, const EpiSpec* epi) {
   wcl_ctx* c0 = ctxs[0];
   const int block = c0->dslash_block[prec];
   DslashArgs a;
@@ -122,6 +130,13 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   a.in = in;
   if (x) a.x = *x;
   if (out2) a.out2 = *out2;
+  if (epi && epi->kind != EPI_NONE) {
+    a.f = epi->f;
+    a.partials = epi->partials;
+    a.counters = epi->counters;
+    a.sc = epi->sc;
+    a.maxch = epi->maxch;
+  }
   a.out_parity = out_parity;
   a.active = active;
   double sites = 0;
@@ -147,6 +162,7 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   if (x) mode |= MODE_XPAY;
   if (x && pre) mode |= MODE_PRE;
   if (out2) mode |= MODE_RECON;
+  if (epi) mode |= epi->kind << 5;
   wcl_ctx::Timed* t = prof_begin(c0);
   cudaError_t e;
   switch (prec) {
@@ -161,7 +177,8 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
     cudaEventRecord(t->b, c0->stream);
     double sp, lk, cl;
     spinor_site_bytes(prec, sp, lk, cl);
-    double per = 8 * lk + 2 * sp + (post ? cl : 0) + (x ? sp : 0) + (x && pre ? cl : 0) + (out2 ? sp : 0);
+    double per = 8 * lk + 2 * sp + (post ? cl : 0) + (x ? sp : 0) + (x && pre ? cl : 0) + (out2 ? sp : 0) +
+                 ((epi && epi->kind == EPI_ALPHA) ? sp : 0);
     // links and clover are shared by the right-hand sides of a site
     double per_site_shared = 8 * lk + (post ? cl : 0) + (x && pre ? cl : 0);
     double per_rhs = per - per_site_shared;
@@ -200,11 +217,13 @@ wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, c
 }
 
 wcl_status apply_mhat(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out_e,
-                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active) {
+                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active,
+                      const EpiSpec* epi) {
   // tmp_o = A_oo^-1 D_oe in_e
   WCL_CHECK(dslash(ctxs, prec, nrhs, tmp_o, in_e, nullptr, 1, dagger, CL_AINV, CL_NONE, C_ONE, C_ZERO, active));
-  // out_e = A_ee in_e - kappa^2 D_eo tmp_o
-  WCL_CHECK(dslash(ctxs, prec, nrhs, out_e, tmp_o, &in_e, 0, dagger, CL_NONE, CL_A, C_MKAPPA2, C_ONE, active));
+  // out_e = A_ee in_e - kappa^2 D_eo tmp_o (+ the fused reduction)
+  WCL_CHECK(dslash_ex(ctxs, prec, nrhs, out_e, tmp_o, &in_e, nullptr, 0, dagger, CL_NONE, CL_A, C_MKAPPA2, C_ONE,
+                      active, epi));
   return WCL_OK;
 }
 

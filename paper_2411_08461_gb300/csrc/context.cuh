@@ -94,6 +94,16 @@ inline double coef_value(Coef c, double kappa) {
 }
 enum CloverSel { CL_NONE = 0, CL_A = 1, CL_AINV = 2 };
 
+// reduction fused into the epilogue of the second launch of M_hat (see DslashEpi)
+struct EpiSpec {
+  int kind = EPI_NONE;
+  FieldRef f{};
+  double* partials = nullptr;  // [slot][maxch][3]
+  unsigned* counters = nullptr;
+  Scalars* sc = nullptr;
+  int maxch = 0;
+};
+
 // out_parity field = C_post(alpha D in + beta C_pre x) on all lattices of the batch
 wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                   const FieldRef* x, int out_parity, bool dagger, CloverSel post, CloverSel pre, Coef alpha,
@@ -102,13 +112,16 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
 // pre = A, x given) out = A^-1 t and out2 = t - A out for t = alpha D in + beta x
 wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                      const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
-                     CloverSel pre, Coef alpha, Coef beta, const int* active);
+                     CloverSel pre, Coef alpha, Coef beta, const int* active, const EpiSpec* epi = nullptr);
+// blocks per (lattice, rhs) slice of a dslash launch (the epilogue partials need this many)
+int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec);
 // out = C x on parity `parity`
 wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out,
                         const FieldRef& x, int parity, CloverSel which, const int* active);
 // M_hat (or its adjoint) in precision prec: out_e = A_ee in_e - kappa^2 D_eo A_oo^-1 D_oe in_e
 wcl_status apply_mhat(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out_e,
-                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active);
+                      const FieldRef& in_e, const FieldRef& tmp_o, bool dagger, const int* active,
+                      const EpiSpec* epi = nullptr);
 // precision conversion of a parity field
 wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrhs, const FieldRef& out,
                    const FieldRef& in, const int* active);

@@ -17,6 +17,7 @@
 //   mu=z: h0 = p0 + s i p2, h1 = p1 - s i p3;  rows 2,3 = -s i h0,  s i h1
 //   mu=t: h0 = p0 + s p2,   h1 = p1 + s p3;    rows 2,3 =  s h0,   s h1
 #pragma once
+#include "blas.cuh"
 #include "internal.cuh"
 
 namespace wcl {
@@ -26,6 +27,14 @@ namespace wcl {
 // solution x_o = A_oo^-1 (b_o + kappa D_oe x_e) and its residual b_o - (A x_o - kappa D x_e)
 // in one pass over the links.
 enum DslashMode { MODE_POST = 1, MODE_XPAY = 2, MODE_PRE = 4, MODE_RECON = 8 };
+
+// Reductions fused into the epilogue of an XPAY launch (the second half of
+// M_hat), finalised on the device like the stand-alone reductions:
+//   EPI_ALPHA   <f, out>              -> BiCGStab alpha = rho / <rhat, v>     (f = rhat)
+//   EPI_OMEGA   <out, x>, ||out||^2   -> BiCGStab omega = <t, s> / <t, t>    (x = s)
+//   EPI_CGALPHA ||out||^2             -> CG alpha = zz / ||q||^2
+//   EPI_CGZ     ||out||^2             -> CG zz' and beta = zz' / zz
+enum DslashEpi { EPI_NONE = 0, EPI_ALPHA = 1, EPI_OMEGA = 2, EPI_CGALPHA = 3, EPI_CGZ = 4 };
 
 struct DslashArgs {
   Batch b;
@@ -38,7 +47,21 @@ struct DslashArgs {
   double alpha[MAXLAT], beta[MAXLAT];
   int out_parity;
   const int* active;  // per slot; null = every slice active
+  // epilogue reduction
+  FieldRef f;
+  double* partials;   // [slot][maxch][3]
+  unsigned* counters; // [slot], zero between launches
+  Scalars* sc;
+  int maxch;
 };
+
+template <int EPI>
+__device__ __forceinline__ void epi_finalize(Scalars& c, const double* t) {
+  if (EPI == EPI_ALPHA) BicgAlpha<F32>{}.finalize(c, t);
+  if (EPI == EPI_OMEGA) BicgOmega<F32>{}.finalize(c, t);
+  if (EPI == EPI_CGALPHA) CgAlpha<F32>{}.finalize(c, t);
+  if (EPI == EPI_CGZ) CgZnorm<F32>{}.finalize(c, t);
+}
 
 template <int MU, int S, typename R>
 __device__ __forceinline__ void project(const cpx<R> p[12], cpx<R> h[6]) {
@@ -126,14 +149,10 @@ __device__ __forceinline__ void hop_dir(cpx<typename Traits<P>::R> acc[12], cons
   reconstruct_acc<MU, SB>(acc, uh);
 }
 
-template <int P, bool DAG, int MODE>
-__global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ DslashArgs a) {
+template <int P, bool DAG, int MODE, int EPI>
+__device__ __forceinline__ void dslash_site(const DslashArgs& a, const Slice& s, const LatGeom& g, long i,
+                                            double red[3]) {
   using R = typename Traits<P>::R;
-  const Slice s = find_slice(a.b, blockIdx.x);
-  if (a.active && !a.active[s.slot]) return;
-  const LatGeom& g = a.b.lat[s.l];
-  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
-  if (i >= g.vh) return;
   const long stride = g.stride;
   const int p = a.out_parity;
 
@@ -212,6 +231,16 @@ __global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ Dsl
 #pragma unroll
       for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
     }
+    if (EPI == EPI_ALPHA) {
+      cpx<R> fv[12];
+      SpinorIO<P>::load(fv, rhs_ptr<P>(a.f, s.l, s.rhs, stride), rhs_norm(a.f, s.l, s.rhs, stride), stride, i);
+      dot_acc(red, fv, acc);
+    } else if (EPI == EPI_OMEGA) {
+      dot_acc(red, acc, xv);
+      red[2] += norm_site(acc);
+    } else if (EPI == EPI_CGALPHA || EPI == EPI_CGZ) {
+      red[0] += norm_site(acc);
+    }
   }
   if (MODE & MODE_POST) {
     cpx<R> y2[12];
@@ -220,6 +249,19 @@ __global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ Dsl
   } else {
     SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, s.rhs, stride), rhs_norm(a.out, s.l, s.rhs, stride), stride, i);
   }
+}
+
+template <int P, bool DAG, int MODE, int EPI>
+__global__ void __launch_bounds__(256) dslash_kernel(const __grid_constant__ DslashArgs a) {
+  const Slice s = find_slice(a.b, blockIdx.x);
+  if (a.active && !a.active[s.slot]) return;
+  const LatGeom& g = a.b.lat[s.l];
+  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
+  double red[3] = {0.0, 0.0, 0.0};
+  if (i < g.vh) dslash_site<P, DAG, MODE, EPI>(a, s, g, i, red);
+  if constexpr (EPI != EPI_NONE)
+    slice_reduce<3>(red, s, g.nchunk, a.maxch, a.partials, a.counters, a.sc,
+                    [](Scalars& c, const double* t) { epi_finalize<EPI>(c, t); });
 }
 
 // Clover-only: out = C x  (used for A_oo^-1 b_o and stand-alone clover applies).
@@ -251,19 +293,27 @@ cudaError_t launch_dslash(const DslashArgs& a, bool dagger, int mode, int block,
 template <int P>
 cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
 
+#define WCL_DSLASH_CASE(P, DAG, MODE, EPI)                                            \
+  case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                       \
+    dslash_kernel<P, DAG, MODE, EPI><<<grid, blk, 0, st>>>(a);                         \
+    break;
+
 #define WCL_DEFINE_DSLASH_LAUNCHERS(P)                                                              \
   template <>                                                                                       \
   cudaError_t launch_dslash<P>(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st) { \
     dim3 grid(a.b.total_blocks), blk(block);                                                        \
-    switch (mode | (dagger ? 16 : 0)) {                                                              \
-      case MODE_POST: dslash_kernel<P, false, MODE_POST><<<grid, blk, 0, st>>>(a); break;            \
-      case MODE_POST | 16: dslash_kernel<P, true, MODE_POST><<<grid, blk, 0, st>>>(a); break;        \
-      case MODE_XPAY | MODE_PRE: dslash_kernel<P, false, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
-      case MODE_XPAY | MODE_PRE | 16: dslash_kernel<P, true, MODE_XPAY | MODE_PRE><<<grid, blk, 0, st>>>(a); break; \
-      case MODE_XPAY: dslash_kernel<P, false, MODE_XPAY><<<grid, blk, 0, st>>>(a); break;            \
-      case MODE_XPAY | MODE_POST: dslash_kernel<P, false, MODE_XPAY | MODE_POST><<<grid, blk, 0, st>>>(a); break; \
-      case MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON:                                           \
-        dslash_kernel<P, false, MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON><<<grid, blk, 0, st>>>(a); break; \
+    switch (mode | (dagger ? 16 : 0)) {                                                             \
+      WCL_DSLASH_CASE(P, false, MODE_POST, EPI_NONE)                                                \
+      WCL_DSLASH_CASE(P, true, MODE_POST, EPI_NONE)                                                 \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_NONE)                                     \
+      WCL_DSLASH_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_NONE)                                      \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_ALPHA)                                    \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_OMEGA)                                    \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_CGALPHA)                                  \
+      WCL_DSLASH_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_CGZ)                                       \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY, EPI_NONE)                                                \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_POST, EPI_NONE)                                    \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON, EPI_NONE)            \
       default: return cudaErrorInvalidValue;                                                        \
     }                                                                                               \
     return cudaGetLastError();                                                                      \

@@ -44,6 +44,9 @@ struct KrylovSolver {
   int* h_upd = nullptr;
   double* d_part = nullptr;
   unsigned* d_cnt = nullptr;
+  double* d_dpart = nullptr;   // dslash-epilogue partials
+  unsigned* d_dcnt = nullptr;
+  int dmaxch = 0;
   Batch bb;  // geometry of the BLAS / reduction launches
   int blk = 256;
 
@@ -79,6 +82,11 @@ struct KrylovSolver {
     d_part = static_cast<double*>(q);
     WCL_CHECK(ws_get(c0, "counters", sizeof(unsigned) * nslot, &q));
     d_cnt = static_cast<unsigned*>(q);
+    dmaxch = dslash_max_chunks(ctxs, S);
+    WCL_CHECK(ws_get(c0, "dpartials", sizeof(double) * nslot * (size_t)dmaxch * 3, &q));
+    d_dpart = static_cast<double*>(q);
+    WCL_CHECK(ws_get(c0, "dcounters", sizeof(unsigned) * nslot, &q));
+    d_dcnt = static_cast<unsigned*>(q);
     WCL_CHECK(hws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
     h_sc = static_cast<Scalars*>(q);
     WCL_CHECK(hws_get(c0, "active", sizeof(int) * 2 * nslot, &q));
@@ -123,22 +131,29 @@ struct KrylovSolver {
     return WCL_OK;
   }
 
+  EpiSpec epi_spec;
+  const EpiSpec* epi(int kind, const FieldRef& f) {
+    epi_spec.kind = kind;
+    epi_spec.f = f;
+    epi_spec.partials = d_dpart;
+    epi_spec.counters = d_dcnt;
+    epi_spec.sc = d_sc;
+    epi_spec.maxch = dmaxch;
+    return &epi_spec;
+  }
+
   // ---- one inner iteration (all active slices) -------------------------------
   wcl_status iteration() {
     if (!cg) {
       WCL_CHECK(map(BicgP<S>{r, p, v, d_sc}, d_active));
-      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active));
-      WCL_CHECK(reduce<2>(BicgAlpha<S>{rhat, v}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active, epi(EPI_ALPHA, rhat)));  // v, alpha
       WCL_CHECK(map(BicgS<S>{r, v, d_sc}, d_active));
-      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, false, d_active));
-      WCL_CHECK(reduce<3>(BicgOmega<S>{t, r}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, false, d_active, epi(EPI_OMEGA, r)));  // t, omega
       WCL_CHECK(reduce<3>(BicgUpdate<S, X>{xs, p, r, t, rhat, d_sc}, d_active));
     } else {
-      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, true, d_active));  // z = M^+ r
-      WCL_CHECK(reduce<1>(CgZnorm<S>{t}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, t, r, tmp, true, d_active, epi(EPI_CGZ, r)));  // z = M^+ r, beta
       WCL_CHECK(map(CgP<S>{t, p, d_sc}, d_active));
-      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active));  // q = M p
-      WCL_CHECK(reduce<1>(CgAlpha<S>{v}, d_active));
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active, epi(EPI_CGALPHA, r)));  // q = M p, alpha
       WCL_CHECK(reduce<1>(CgUpdate<S, X>{xs, p, r, v, d_sc}, d_active));
     }
     return WCL_OK;
