@@ -76,7 +76,8 @@ typedef enum { WCL_F64 = 0, WCL_F32 = 1, WCL_F16 = 2, WCL_BF16 = 3 } wcl_prec;
 typedef enum {
   WCL_BICGSTAB = 0,      /* BiCGStab on M_hat (Sec. II.E: default for clover) */
   WCL_CGNR = 1,          /* CG on M_hat^+ M_hat (Sec. II.E: CG) */
-  WCL_FGCR_LEARNED = 2   /* flexible GCR on M_hat with the learned preconditioner */
+  WCL_FGCR_LEARNED = 2,  /* flexible GCR on M_hat with the learned preconditioner */
+  WCL_GCR = 3            /* the same GCR without a preconditioner (the comparison method) */
 } wcl_solver;
 
 typedef struct {
@@ -150,6 +151,53 @@ wcl_status wcl_invert(wcl_ctx* ctx, void* d_x, const void* d_b, int nrhs,
  *   info: host array of nctx * nrhs entries, lattice-major. */
 wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, const void* const* d_b, int nrhs,
                             const wcl_solve_params* params, wcl_solve_info* info);
+
+/* ---- learned preconditioner ------------------------------------------------
+ * Not part of the paper: a gauge-covariant parallel-transport network N used as
+ * the preconditioner of flexible GCR (WCL_FGCR_LEARNED).  Four linear layers with
+ * channels 1 -> 4 -> 4 -> 4 -> 1,
+ *   out_{c'}(x) = sum_{c,s} W[c',c,s] (T_s in_c)(x),  s in {0, +x, -x, +y, -y, +z, -z, +t, -t},
+ *   T_0 = 1, T_{+mu} psi(x) = eta U_mu(x) psi(x+mu), T_{-mu} psi(x) = eta U_mu(x-mu)^+ psi(x-mu),
+ * W[c',c,s] a complex 4x4 spin matrix.  It acts on even-parity fields (the odd
+ * sites of its input are zero; the even part of its output approximates
+ * M_hat^-1 r), so the weights do not depend on the gauge field or the volume.
+ * Weights: WCL_PTC_NWEIGHTS complex numbers, layer by layer, each layer indexed
+ * ((c_out * c_in + c_in_index) * 9 + s) * 16 + 4 * row + col, shifts ordered
+ * 0, +x, -x, +y, -y, +z, -z, +t, -t.  Host arrays are interleaved (re, im) doubles. */
+#define WCL_PTC_NWEIGHTS 5760
+
+typedef struct {
+  int epochs;   /* passes over the pairs */
+  int batch;    /* pairs per Adam step */
+  double lr, beta1, beta2, eps; /* Adam on real and imaginary parts */
+} wcl_train_params;
+
+/* Defaults: 4 epochs, batch 8, Adam lr 1e-3, betas 0.9 / 0.999, eps 1e-8. */
+void wcl_default_train_params(wcl_train_params* p);
+
+/* Copy WCL_PTC_NWEIGHTS complex weights (host, interleaved doubles) to ctx; resets Adam. */
+wcl_status wcl_precond_load(wcl_ctx* ctx, const double* h_weights);
+
+/* Copy the current FP32 master weights of ctx back to the host. */
+wcl_status wcl_precond_get(wcl_ctx* ctx, double* h_weights);
+
+/* d_out_e = N(d_in_e) for nrhs even half-fields (QDP even half, complex128);
+ * bf16 != 0 uses the BF16 copy of the weights (FP32 accumulation either way). */
+wcl_status wcl_precond_apply(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, int nrhs, int bf16);
+
+/* Loss L = (1/n) sum_b ||N(r_b)_e - e_b||^2 / ||e_b||^2 over n pairs of even
+ * half-fields (device, [n][even half] complex128) and its gradient with respect
+ * to every weight, G = dL/dRe W + i dL/dIm W (host array, interleaved doubles,
+ * may be NULL), using the FP32 weights. */
+wcl_status wcl_precond_loss_grad(wcl_ctx* ctx, const void* d_r_e, const void* d_e_e, int npairs, double* loss,
+                                 double* h_grad);
+
+/* Train the weights of ctx with Adam on n pairs (r, e), r = M_hat e (device,
+ * [n][even half] complex128).  Forward, backward and update run on the GPU with
+ * this library's kernels.  h_loss_per_epoch (host, epochs entries, may be NULL)
+ * receives the mean batch loss of every epoch. */
+wcl_status wcl_precond_train(wcl_ctx* ctx, const void* d_r_e, const void* d_e_e, int npairs,
+                             const wcl_train_params* params, double* h_loss_per_epoch);
 
 /* Counters for measurement. */
 typedef struct {

@@ -107,15 +107,22 @@ def forward(U, weights, r, t_boundary=-1):
     return acts[-1][0], acts
 
 
-def loss_and_grad(U, weights, rs, es, t_boundary=-1):
-    """Relative squared error averaged over the batch, and G_W for every layer."""
+def loss_and_grad(U, weights, rs, es, t_boundary=-1, mask=None):
+    """Relative squared error averaged over the batch, and G_W for every layer.
+
+    With a site mask (boolean (Lt, Lz, Ly, Lx)), only the masked sites of the
+    output enter the loss: the even-odd form of the preconditioner, whose input
+    is an even-parity field and whose even output approximates M_hat^-1 r.
+    """
     nb = len(rs)
     total = 0.0
     grads = [np.zeros_like(W) for W in weights]
+    m = 1.0 if mask is None else mask[..., None, None]
     for r, e in zip(rs, es):
         out, acts = forward(U, weights, r, t_boundary)
+        e = e * m
         en = float(np.vdot(e, e).real)
-        diff = out - e
+        diff = (out - e) * m
         total += float(np.vdot(diff, diff).real) / en / nb
         g = (2.0 / en / nb) * diff[None]
         for li in range(len(weights) - 1, -1, -1):

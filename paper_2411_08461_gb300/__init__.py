@@ -9,6 +9,9 @@ from .wcl import (  # noqa: F401
     WclError,
     load_library,
     wcl_default_params,
+    ptc_flatten,
+    ptc_unflatten,
+    wcl_default_train_params,
     wcl_invert_batch,
     wcl_status_string,
 )

@@ -14,10 +14,12 @@ wcl_status krylov_solve(const std::vector<wcl_ctx*>& ctxs, int nrhs, const wcl_s
 
 using namespace wcl;
 
-namespace {
+namespace wcl {
+void ptc_free(wcl_ctx* c);
+}
 
 // order the call after the caller's pending work, run on the internal stream
-wcl_status enter(wcl_ctx* c) {
+wcl_status wcl_enter(wcl_ctx* c) {
   WCL_CUDA(cudaSetDevice(c->device));
   WCL_CUDA(cudaEventRecord(c->ev_in, c->user_stream));
   WCL_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
@@ -25,7 +27,7 @@ wcl_status enter(wcl_ctx* c) {
   return WCL_OK;
 }
 
-wcl_status leave(wcl_ctx* c, wcl_status s) {
+wcl_status wcl_leave(wcl_ctx* c, wcl_status s) {
   // later work on the caller's stream is ordered after this call's work
   cudaError_t e = cudaEventRecord(c->ev_out, c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->user_stream, c->ev_out, 0);
@@ -33,6 +35,11 @@ wcl_status leave(wcl_ctx* c, wcl_status s) {
   if (e != cudaSuccess && s == WCL_OK) return cuda_fail(e, "cudaStreamSynchronize");
   return s;
 }
+
+namespace {
+
+wcl_status enter(wcl_ctx* c) { return wcl_enter(c); }
+wcl_status leave(wcl_ctx* c, wcl_status s) { return wcl_leave(c, s); }
 
 bool valid_prec(int p) { return p >= WCL_F64 && p <= WCL_BF16; }
 
@@ -301,7 +308,7 @@ static wcl_status check_params(const wcl_solve_params* p) {
     set_error("invalid solve parameters (outer must be F64, 0 < delta < 1, tol > 0)");
     return WCL_ERR_INVALID_ARG;
   }
-  if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED) {
+  if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED && p->solver != WCL_GCR) {
     set_error("unknown solver %d", (int)p->solver);
     return WCL_ERR_INVALID_ARG;
   }
@@ -310,8 +317,8 @@ static wcl_status check_params(const wcl_solve_params* p) {
 
 static wcl_status solve(const std::vector<wcl_ctx*>& v, int nrhs, const wcl_solve_params* p, void* const* d_x,
                         const void* const* d_b, wcl_solve_info* info) {
-  if (p->solver == WCL_FGCR_LEARNED) {
-    set_error("learned FGCR: no preconditioner weights loaded");
+  if (p->solver == WCL_FGCR_LEARNED && !v[0]->ptc.loaded) {
+    set_error("learned FGCR: no preconditioner weights loaded (wcl_precond_load / wcl_precond_train)");
     return WCL_ERR_NO_PRECOND;
   }
   SolveIO io{d_x, d_b};
@@ -408,6 +415,7 @@ wcl_status wcl_destroy(wcl_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_lattice(c);
+  ptc_free(c);
   for (auto& kv : c->ws) cudaFree(kv.second.p);
   for (auto& kv : c->hws) cudaFreeHost(kv.second.p);
   for (auto& t : c->ev_pool) {

@@ -515,3 +515,139 @@ struct ResetCg {  // forget the CG search direction scale (beta = 0 on the next 
 };
 
 }  // namespace wcl
+
+namespace wcl {
+
+// ---------------------------------------------------------------------------
+// Flexible GCR helpers.  The Krylov sets Z, W hold m vectors of nrhs parity
+// fields each: vector j of lattice l starts vstride[l] bytes after vector j-1.
+constexpr int GCR_MAXK = 20;
+
+template <int S>
+__device__ __forceinline__ const void* kry_ptr(const FieldRef& base, const long* vstride, int j, int l, int rhs,
+                                                long stride) {
+  return static_cast<const char*>(rhs_ptr<S>(base, l, rhs, stride)) + (size_t)j * vstride[l];
+}
+template <int S>
+__device__ __forceinline__ void* kry_ptr_w(const FieldRef& base, const long* vstride, int j, int l, int rhs,
+                                           long stride) {
+  return static_cast<char*>(rhs_ptr_w<S>(base, l, rhs, stride)) + (size_t)j * vstride[l];
+}
+__device__ __forceinline__ float* kry_norm(const FieldRef& base, const long* nvstride, int j, int l, int rhs,
+                                           long stride) {
+  return base.norm[l] ? base.norm[l] + (size_t)rhs * stride + (size_t)j * nvstride[l] : nullptr;
+}
+
+// beta_j = <W_j, w> for j < k; stored in betas[slot * GCR_MAXK + j]
+template <int S>
+struct GcrMultiDot {
+  FieldRef W, w;
+  long vstride[MAXLAT], nvstride[MAXLAT];
+  int k;
+  double2* betas;
+  const Scalars* sc_base;
+  __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
+    cpx<typename Traits<S>::R> a[12], b[12];
+    WCL_LD(S, true, b, w);
+    for (int j = 0; j < k; j++) {
+      SpinorIO<S>::load(a, kry_ptr<S>(W, vstride, j, s.l, s.rhs, g.stride), kry_norm(W, nvstride, j, s.l, s.rhs, g.stride),
+                        g.stride, i);
+      double d[2] = {0, 0};
+      dot_acc(d, a, b);
+      acc[2 * j] += d[0];
+      acc[2 * j + 1] += d[1];
+    }
+  }
+  __device__ void finalize(Scalars& c, const double* t) const {
+    const long slot = &c - sc_base;
+    for (int j = 0; j < k; j++) betas[slot * GCR_MAXK + j] = make_double2(t[2 * j], t[2 * j + 1]);
+  }
+};
+
+// w -= sum_j beta_j W_j ; z -= sum_j beta_j Z_j
+template <int S>
+struct GcrMultiAxpy {
+  FieldRef W, Z, w, z;
+  long vstride[MAXLAT], nvstride[MAXLAT];
+  int k;
+  const double2* betas;
+  __device__ void operator()(const Slice& s, const LatGeom& g, long i) const {
+    using R = typename Traits<S>::R;
+    cpx<R> ww[12], zz[12], a[12];
+    WCL_LD(S, false, ww, w);
+    WCL_LD(S, false, zz, z);
+    for (int j = 0; j < k; j++) {
+      const double2 bj = betas[s.slot * GCR_MAXK + j];
+      const cpx<R> b = {R(bj.x), R(bj.y)};
+      SpinorIO<S>::load(a, kry_ptr<S>(W, vstride, j, s.l, s.rhs, g.stride), kry_norm(W, nvstride, j, s.l, s.rhs, g.stride),
+                        g.stride, i);
+#pragma unroll
+      for (int c = 0; c < 12; c++) ww[c] = ww[c] - b * a[c];
+      SpinorIO<S>::load(a, kry_ptr<S>(Z, vstride, j, s.l, s.rhs, g.stride), kry_norm(Z, nvstride, j, s.l, s.rhs, g.stride),
+                        g.stride, i);
+#pragma unroll
+      for (int c = 0; c < 12; c++) zz[c] = zz[c] - b * a[c];
+    }
+    WCL_ST(S, ww, w);
+    WCL_ST(S, zz, z);
+  }
+};
+
+// alpha = <w, r> / ||w||^2, aux[4] = 1 / ||w||
+template <int S>
+struct GcrAlpha {
+  FieldRef w, r;
+  __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
+    cpx<typename Traits<S>::R> a[12], b[12];
+    WCL_LD(S, true, a, w);
+    WCL_LD(S, true, b, r);
+    dot_acc(acc, a, b);
+    acc[2] += norm_site(a);
+  }
+  __device__ void finalize(Scalars& c, const double* t) const {
+    if (!(t[2] > 0.0)) {
+      c.alpha = make_double2(0, 0);
+      c.aux[4] = 0.0;
+      c.flags |= 1;
+    } else {
+      c.alpha = make_double2(t[0] / t[2], t[1] / t[2]);
+      c.aux[4] = 1.0 / sqrt(t[2]);
+    }
+  }
+};
+
+// x += alpha z; r -= alpha w; then w, z scaled to unit ||w||; r2 = ||r||^2
+template <int S, int X>
+struct GcrUpdate {
+  FieldRef xs, r, w, z;
+  const Scalars* sc;
+  __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
+    using R = typename Traits<S>::R;
+    using RX = typename Traits<X>::R;
+    const double2 a2 = sc[s.slot].alpha;
+    const R inv = R(sc[s.slot].aux[4]);
+    const cpx<R> al = {R(a2.x), R(a2.y)};
+    const cpx<RX> ax = {RX(a2.x), RX(a2.y)};
+    cpx<R> rr[12], ww[12], zz[12];
+    cpx<RX> xx[12];
+    WCL_LD(S, false, rr, r);
+    WCL_LD(S, false, ww, w);
+    WCL_LD(S, false, zz, z);
+    WCL_LD(X, false, xx, xs);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      xx[c] = xx[c] + ax * cpx<RX>{RX(zz[c].re), RX(zz[c].im)};
+      rr[c] = rr[c] - al * ww[c];
+      ww[c] = inv * ww[c];
+      zz[c] = inv * zz[c];
+    }
+    WCL_ST(X, xx, xs);
+    WCL_ST(S, rr, r);
+    WCL_ST(S, ww, w);
+    WCL_ST(S, zz, z);
+    acc[0] += norm_site(rr);
+  }
+  __device__ void finalize(Scalars& c, const double* t) const { c.r2 = t[0]; }
+};
+
+}  // namespace wcl

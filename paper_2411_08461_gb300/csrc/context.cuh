@@ -39,6 +39,17 @@ struct wcl_ctx {
   bool capturing = false;
   long long capture_launches = 0, capture_dslash = 0;
 
+  // learned preconditioner (PTC network) weights, device copies
+  struct Ptc {
+    float2* w32 = nullptr;          // FP32 complex master weights
+    __nv_bfloat162* w16 = nullptr;  // BF16 copy used for inference
+    float2* m = nullptr;            // Adam moments (re, im treated separately)
+    float2* v = nullptr;
+    double2* grad = nullptr;        // last gradient (dL/dRe + i dL/dIm)
+    int steps = 0;
+    bool loaded = false;
+  } ptc;
+
   // launch shapes (picked by the tuner on first use)
   int dslash_block[4] = {128, 128, 128, 128};
   int blas_block = 256;

@@ -1,0 +1,223 @@
+// PTC network layer and weight-gradient kernels (see ptc.cuh).
+#include "ptc.cuh"
+
+namespace wcl {
+
+// T_s psi at output site i of parity p (input on parity 1-p for s != 0).
+// s = 0: identity; s = 1 + 2 mu: +mu; s = 2 + 2 mu: -mu.
+struct Nbr {
+  long jf[4], jb[4];
+  float sf, sb;  // time-boundary signs of the t hops
+};
+
+__device__ __forceinline__ Nbr neighbours(const LatGeom& g, int p, long i) {
+  Nbr n;
+  const int lxh = g.lxh, Lx = g.dims[0], Ly = g.dims[1], Lz = g.dims[2], Lt = g.dims[3];
+  const int xh = (int)(i % lxh);
+  int rem = (int)(i / lxh);
+  const int y = rem % Ly;
+  rem /= Ly;
+  const int z = rem % Lz;
+  const int t = rem / Lz;
+  const int x = 2 * xh + ((p + y + z + t) & 1);
+  const long row = i - xh;
+  const long plane = (long)lxh * Ly, vol3 = plane * Lz;
+  n.jf[0] = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
+  n.jb[0] = row + ((x == 0 ? Lx - 1 : x - 1) >> 1);
+  n.jf[1] = (y + 1 == Ly) ? i - (long)(Ly - 1) * lxh : i + lxh;
+  n.jb[1] = (y == 0) ? i + (long)(Ly - 1) * lxh : i - lxh;
+  n.jf[2] = (z + 1 == Lz) ? i - (long)(Lz - 1) * plane : i + plane;
+  n.jb[2] = (z == 0) ? i + (long)(Lz - 1) * plane : i - plane;
+  n.jf[3] = (t + 1 == Lt) ? i - (long)(Lt - 1) * vol3 : i + vol3;
+  n.jb[3] = (t == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3;
+  n.sf = (t + 1 == Lt) ? g.tb : 1.f;
+  n.sb = (t == 0) ? g.tb : 1.f;
+  return n;
+}
+
+__device__ __forceinline__ void transport(cpx<float> out[12], int s, const float4* f_here, const float4* f_there,
+                                          const void* g_here, const void* g_there, long stride, long i,
+                                          const Nbr& n) {
+  if (s == 0) {
+    SpinorIO<F32>::load(out, f_here, nullptr, stride, i);
+    return;
+  }
+  const int mu = (s - 1) >> 1;
+  const bool back = ((s - 1) & 1) != 0;
+  cpx<float> psi[12], u[3][3];
+  if (!back) {
+    SpinorIO<F32>::load(psi, f_there, nullptr, stride, n.jf[mu]);
+    LinkIO<F32>::load(u, g_here, stride, i, mu);
+    const float sg = (mu == 3) ? n.sf : 1.f;
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        cpx<float> acc = {0, 0};
+#pragma unroll
+        for (int b = 0; b < 3; b++) cfma(acc, u[a][b], psi[3 * sp + b]);
+        out[3 * sp + a] = sg * acc;
+      }
+  } else {
+    SpinorIO<F32>::load(psi, f_there, nullptr, stride, n.jb[mu]);
+    LinkIO<F32>::load(u, g_there, stride, n.jb[mu], mu);
+    const float sg = (mu == 3) ? n.sb : 1.f;
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        cpx<float> acc = {0, 0};
+#pragma unroll
+        for (int b = 0; b < 3; b++) cfma_conj(acc, u[b][a], psi[3 * sp + b]);
+        out[3 * sp + a] = sg * acc;
+      }
+  }
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(128) ptc_layer_kernel(const __grid_constant__ PtcLayerArgs a) {
+  __shared__ float2 w_s[PTC_MAXC * PTC_MAXC * PTC_NSHIFT * 16];
+  const int nw = a.cout * a.cin * PTC_NSHIFT * 16;
+  for (int k = threadIdx.x; k < nw; k += blockDim.x) {
+    if (a.use_bf16) {
+      float2 v = __bfloat1622float2(a.wb[k]);
+      w_s[k] = v;
+    } else {
+      w_s[k] = a.w[k];
+    }
+  }
+  __syncthreads();
+  const Slice s = find_slice(a.b, blockIdx.x);
+  const LatGeom& g = a.b.lat[s.l];
+  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
+  if (i >= g.vh) return;
+  const long stride = g.stride;
+  const int p = a.parity;
+  const Nbr n = neighbours(g, p, i);
+  const void* g_here = a.gauge[s.l][p];
+  const void* g_there = a.gauge[s.l][1 - p];
+
+  cpx<float> acc[COUT][12];
+#pragma unroll
+  for (int co = 0; co < COUT; co++)
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[co][k] = {0.f, 0.f};
+
+  for (int ci = 0; ci < a.cin; ci++) {
+    const float4* f_here = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, p, stride);
+    const float4* f_there = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, 1 - p, stride);
+#pragma unroll
+    for (int sh = 0; sh < PTC_NSHIFT; sh++) {
+      cpx<float> t[12];
+      transport(t, sh, f_here, f_there, g_here, g_there, stride, i, n);
+#pragma unroll
+      for (int co = 0; co < COUT; co++) {
+        const float2* w = w_s + ((co * a.cin + ci) * PTC_NSHIFT + sh) * 16;
+#pragma unroll
+        for (int al = 0; al < 4; al++)
+#pragma unroll
+          for (int be = 0; be < 4; be++) {
+            const float2 wv = w[al * 4 + be];
+            const cpx<float> wc = {wv.x, wv.y};
+#pragma unroll
+            for (int col = 0; col < 3; col++) cfma(acc[co][3 * al + col], wc, t[3 * be + col]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int co = 0; co < COUT; co++) {
+    float4* o = a.out[s.l] + ptc_field_offset(s.rhs, co, COUT, p, stride);
+    if (a.accumulate) {
+      cpx<float> prev[12];
+      SpinorIO<F32>::load<false>(prev, o, nullptr, stride, i);
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[co][k] = acc[co][k] + prev[k];
+    }
+    SpinorIO<F32>::store(acc[co], o, nullptr, stride, i);
+  }
+}
+
+cudaError_t ptc_layer(const PtcLayerArgs& a, int block, cudaStream_t st) {
+  if (a.cout == 1)
+    ptc_layer_kernel<1><<<a.b.total_blocks, block, 0, st>>>(a);
+  else if (a.cout == 4)
+    ptc_layer_kernel<4><<<a.b.total_blocks, block, 0, st>>>(a);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: block (slice chunk, ci*9 + s); every thread sums its sites
+// of G_co(x) (T_s in_ci)(x)^+ into 16*COUT complex registers, the block reduces
+template <int COUT>
+__global__ void __launch_bounds__(128) ptc_grad_kernel(const __grid_constant__ PtcGradArgs a) {
+  const Slice s = find_slice(a.b, blockIdx.x);
+  const LatGeom& g = a.b.lat[s.l];
+  const int cs = blockIdx.y;  // ci * 9 + shift
+  const int ci = cs / PTC_NSHIFT, sh = cs % PTC_NSHIFT;
+  const long stride = g.stride;
+  const int p = a.parity;
+  const void* g_here = a.gauge[s.l][p];
+  const void* g_there = a.gauge[s.l][1 - p];
+  const float4* f_here = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, p, stride);
+  const float4* f_there = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, 1 - p, stride);
+
+  float acc[COUT * 32];
+#pragma unroll
+  for (int k = 0; k < COUT * 32; k++) acc[k] = 0.f;
+  for (long i = (long)s.chunk * blockDim.x + threadIdx.x; i < g.vh; i += (long)g.nchunk * blockDim.x) {
+    const Nbr n = neighbours(g, p, i);
+    cpx<float> t[12];
+    transport(t, sh, f_here, f_there, g_here, g_there, stride, i, n);
+#pragma unroll
+    for (int co = 0; co < COUT; co++) {
+      cpx<float> gv[12];
+      SpinorIO<F32>::load(gv, a.g[s.l] + ptc_field_offset(s.rhs, co, COUT, p, stride), nullptr, stride, i);
+#pragma unroll
+      for (int al = 0; al < 4; al++)
+#pragma unroll
+        for (int be = 0; be < 4; be++) {
+          cpx<float> v = {acc[co * 32 + (al * 4 + be) * 2], acc[co * 32 + (al * 4 + be) * 2 + 1]};
+#pragma unroll
+          for (int col = 0; col < 3; col++) cfma_conj(v, t[3 * be + col], gv[3 * al + col]);
+          acc[co * 32 + (al * 4 + be) * 2] = v.re;
+          acc[co * 32 + (al * 4 + be) * 2 + 1] = v.im;
+        }
+    }
+  }
+  // block reduction: warp shuffles, then one partial per block in FP64
+  __shared__ double sh_acc[4][PTC_MAXC * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < COUT * 32; k++) {
+    float v = acc[k];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh_acc[warp][k] = v;
+  }
+  __syncthreads();
+  double2* dst = a.partials + (((size_t)s.slot * (a.cin * PTC_NSHIFT) + cs) * a.maxch + s.chunk) * (COUT * 16);
+  for (int k = threadIdx.x; k < COUT * 16; k += blockDim.x) {
+    double re = 0, im = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      re += sh_acc[w][2 * k];
+      im += sh_acc[w][2 * k + 1];
+    }
+    dst[k] = make_double2(re, im);
+  }
+}
+
+cudaError_t ptc_grad(const PtcGradArgs& a, int block, cudaStream_t st) {
+  dim3 grid(a.b.total_blocks, a.cin * PTC_NSHIFT);
+  if (a.cout == 1)
+    ptc_grad_kernel<1><<<grid, block, 0, st>>>(a);
+  else if (a.cout == 4)
+    ptc_grad_kernel<4><<<grid, block, 0, st>>>(a);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace wcl

@@ -24,6 +24,8 @@
 
 namespace wcl {
 
+wcl_status ptc_apply(const std::vector<wcl_ctx*>& ctxs, int nrhs, const FieldRef& r, const FieldRef& z, int use_bf16);
+
 template <int S>
 struct KrylovSolver {
   static constexpr int X = (S == F64) ? F64 : F32;  // precision of the sloppy solution accumulator
@@ -32,6 +34,7 @@ struct KrylovSolver {
   int nrhs = 0, nslot = 0;
   wcl_solve_params prm;
   bool cg = false;
+  bool gcr = false;
 
   FieldRef b_e, b_o, bhat, x, x_o, r64, tmp64;  // FP64
   FieldRef r, rhat, p, v, t, tmp;               // sloppy
@@ -78,7 +81,7 @@ struct KrylovSolver {
     WCL_CHECK(ws_get(c0, "active", sizeof(int) * 2 * nslot, &q));
     d_active = static_cast<int*>(q);
     d_upd = d_active + nslot;
-    WCL_CHECK(ws_get(c0, "partials", sizeof(double) * nslot * RED_MAXCH * 4, &q));
+    WCL_CHECK(ws_get(c0, "partials", sizeof(double) * nslot * RED_MAXCH * 2 * GCR_MAXK, &q));
     d_part = static_cast<double*>(q);
     WCL_CHECK(ws_get(c0, "counters", sizeof(unsigned) * nslot, &q));
     d_cnt = static_cast<unsigned*>(q);
@@ -235,12 +238,146 @@ struct KrylovSolver {
     }
   }
 
+  // ---- flexible GCR on M_hat (restarted every m steps) ------------------------
+  // z_k = N(r) (the learned network, or z_k = r for plain GCR), w_k = M_hat z_k,
+  // w_k and z_k orthogonalised against W by classical Gram-Schmidt applied twice
+  // (as stable as modified Gram-Schmidt, two passes instead of k), then
+  // alpha = <w_k, r>/||w_k||^2, x += alpha z_k, r -= alpha w_k, and w_k, z_k
+  // rescaled to unit ||w_k||.  Every restart is a reliable update.
+  wcl_status loop_gcr(int& nactive, bool learned) {
+    const int m = std::min(std::max(1, prm.gcr_nkrylov), GCR_MAXK);
+    FieldRef Z{}, W{}, r32{}, z32{};
+    long vstride[MAXLAT] = {}, nvstride[MAXLAT] = {};
+    const bool half = (S == F16 || S == BF16);
+    for (size_t l = 0; l < ctxs.size(); l++) {
+      wcl_ctx* c = ctxs[l];
+      const long st = c->lat.stride;
+      const size_t chunk = (size_t)nrhs * spinor_field_bytes(S, st);
+      const size_t nb = half ? (size_t)nrhs * st * sizeof(float) : 0;
+      const size_t blockb = (chunk + nb + 255) / 256 * 256;
+      void *pz, *pw;
+      WCL_CHECK(ws_get(c, "gcr_Z" + std::to_string(S), blockb * m, &pz));
+      WCL_CHECK(ws_get(c, "gcr_W" + std::to_string(S), blockb * m, &pw));
+      Z.ptr[l] = pz;
+      W.ptr[l] = pw;
+      Z.norm[l] = half ? reinterpret_cast<float*>(static_cast<char*>(pz) + chunk) : nullptr;
+      W.norm[l] = half ? reinterpret_cast<float*>(static_cast<char*>(pw) + chunk) : nullptr;
+      vstride[l] = (long)blockb;
+      nvstride[l] = (long)(blockb / sizeof(float));
+    }
+    auto vec = [&](const FieldRef& base, int j) {
+      FieldRef f{};
+      for (size_t l = 0; l < ctxs.size(); l++) {
+        f.ptr[l] = static_cast<char*>(base.ptr[l]) + (size_t)j * vstride[l];
+        f.norm[l] = base.norm[l] ? base.norm[l] + (size_t)j * nvstride[l] : nullptr;
+      }
+      return f;
+    };
+    if (learned && S != F32) {
+      WCL_CHECK(ws_field(ctxs, "gcr_r32", F32, nrhs, &r32));
+      WCL_CHECK(ws_field(ctxs, "gcr_z32", F32, nrhs, &z32));
+    }
+    void* q;
+    WCL_CHECK(ws_get(c0, "gcr_betas", sizeof(double2) * nslot * GCR_MAXK, &q));
+    double2* betas = static_cast<double2*>(q);
+    const double d2 = prm.delta_reliable * prm.delta_reliable;
+    int k = 0;
+    while (nactive > 0) {
+      const FieldRef Zk = vec(Z, k), Wk = vec(W, k);
+      if (learned) {
+        if (S == F32) {
+          WCL_CHECK(ptc_apply(ctxs, nrhs, r, Zk, 1));
+        } else {
+          WCL_CHECK(convert(ctxs, F32, S, nrhs, r32, r, d_active));
+          WCL_CHECK(ptc_apply(ctxs, nrhs, r32, z32, 1));
+          WCL_CHECK(convert(ctxs, S, F32, nrhs, Zk, z32, d_active));
+        }
+      } else {
+        WCL_CHECK(convert(ctxs, S, S, nrhs, Zk, r, d_active));
+      }
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, Wk, Zk, tmp, false, d_active));
+      for (int pass = 0; pass < 2 && k > 0; pass++) {
+        GcrMultiDot<S> md{};
+        md.W = W;
+        md.w = Wk;
+        md.k = k;
+        md.betas = betas;
+        md.sc_base = d_sc;
+        GcrMultiAxpy<S> ma{};
+        ma.W = W;
+        ma.Z = Z;
+        ma.w = Wk;
+        ma.z = Zk;
+        ma.k = k;
+        ma.betas = betas;
+        for (size_t l = 0; l < ctxs.size(); l++) {
+          md.vstride[l] = ma.vstride[l] = vstride[l];
+          md.nvstride[l] = ma.nvstride[l] = nvstride[l];
+        }
+        WCL_CHECK(reduce<2 * GCR_MAXK>(md, d_active));
+        WCL_CHECK(map(ma, d_active));
+      }
+      WCL_CHECK(reduce<3>(GcrAlpha<S>{Wk, r}, d_active));
+      WCL_CHECK(reduce<1>(GcrUpdate<S, X>{xs, r, Wk, Zk, d_sc}, d_active));
+      k++;
+      WCL_CHECK(sync_scalars());
+      profile_sync();
+      bool any = false;
+      for (int s = 0; s < nslot; s++) {
+        h_upd[s] = 0;
+        if (!h_active[s]) continue;
+        iters[s] += 1;
+        const double r2 = h_sc[s].r2;
+        r2max[s] = std::max(r2max[s], r2);
+        const bool brk = (h_sc[s].flags & 1) || !(r2 == r2);
+        if (k == m || r2 <= stop2[s] || r2 < d2 * r2max[s] || brk || iters[s] >= prm.maxiter) any = true;
+      }
+      if (!any) continue;
+      for (int s = 0; s < nslot; s++) h_upd[s] = h_active[s];
+      WCL_CHECK(push_masks());
+      WCL_CHECK(reliable_update(false));
+      WCL_CHECK(sync_scalars());
+      profile_sync();
+      for (int s = 0; s < nslot; s++) {
+        if (!h_upd[s]) continue;
+        updates[s]++;
+        const double tr2 = h_sc[s].aux[3];
+        r2max[s] = h_sc[s].aux[0];
+        if (!(tr2 == tr2) || std::isinf(tr2)) {
+          status[s] = WCL_ERR_NONFINITE;
+          h_active[s] = 0;
+          nactive--;
+        } else if (tr2 <= stop2[s]) {
+          h_active[s] = 0;
+          nactive--;
+        } else if (iters[s] >= prm.maxiter) {
+          status[s] = WCL_ERR_NOT_CONVERGED;
+          h_active[s] = 0;
+          nactive--;
+        } else if (h_sc[s].flags & 1) {
+          if (++restarts[s] > 3) {
+            status[s] = WCL_ERR_BREAKDOWN;
+            h_active[s] = 0;
+            nactive--;
+          }
+        }
+        h_sc[s].flags = 0;
+      }
+      for (int s = 0; s < nslot; s++) h_upd[s] = 0;
+      WCL_CUDA(cudaMemcpyAsync(d_sc, h_sc, sizeof(Scalars) * nslot, cudaMemcpyHostToDevice, c0->stream));
+      WCL_CHECK(push_masks());
+      k = 0;  // restart from the replaced residual
+    }
+    return WCL_OK;
+  }
+
   // ---- the whole solve -------------------------------------------------------
   wcl_status run(const SolveIO& io, wcl_solve_info* info) {
     auto t0 = std::chrono::steady_clock::now();
     c0 = ctxs[0];
     nslot = (int)ctxs.size() * nrhs;
-    cg = prm.solver == WCL_CGNR;
+    gcr = prm.solver == WCL_FGCR_LEARNED || prm.solver == WCL_GCR;
+    cg = prm.solver == WCL_CGNR || gcr;  // GCR residual replacement keeps no BiCGStab state
     blk = c0->blas_block;
     bb = make_batch(ctxs, nrhs, blk, RED_MAXCH);
     WCL_CHECK(alloc());
@@ -302,6 +439,7 @@ struct KrylovSolver {
 
     const int ce = std::max(1, prm.check_every);
     const double d2 = prm.delta_reliable * prm.delta_reliable;
+    if (gcr) WCL_CHECK(loop_gcr(nactive, prm.solver == WCL_FGCR_LEARNED));
     // events inside captured graphs cannot be timed: profiling launches directly
     bool graphs = prm.use_graphs != 0 && !c0->profiling;
     while (nactive > 0) {

@@ -21,7 +21,9 @@ STATUS_NAMES = {
     9: "WCL_ERR_NO_GAUGE", 10: "WCL_ERR_NO_PRECOND",
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
-SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2}
+SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3}
+PTC_NWEIGHTS = 5760
+PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 
 class wcl_solve_params(ctypes.Structure):
@@ -44,6 +46,11 @@ class wcl_stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong), ("dslash_launches", ctypes.c_longlong), ("dslash_ms", ctypes.c_double),
         ("dslash_timed", ctypes.c_longlong), ("dslash_bytes", ctypes.c_double), ("dslash_flops", ctypes.c_double),
     ]
+
+
+class wcl_train_params(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
 class WclError(RuntimeError):
@@ -70,6 +77,14 @@ SIGNATURES = {
     "wcl_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "wcl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(wcl_stats), ctypes.c_int]),
     "wcl_apply_Mpc_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "wcl_default_train_params": (None, [ctypes.POINTER(wcl_train_params)]),
+    "wcl_precond_load": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "wcl_precond_get": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "wcl_precond_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
+    "wcl_precond_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "wcl_precond_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_train_params),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -198,6 +213,61 @@ class Context:
             _check(st, "wcl_invert")
         return st, [_info_dict(i) for i in info]
 
+    # ---- learned preconditioner (weights are host numpy complex128, WCL_PTC_NWEIGHTS) ----
+    def wcl_precond_load(self, weights):
+        import numpy as np
+
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128).ravel())
+        if w.size != PTC_NWEIGHTS:
+            raise ValueError(f"expected {PTC_NWEIGHTS} complex weights, got {w.size}")
+        buf = w.view(np.float64)
+        _check(load_library().wcl_precond_load(self.handle, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_precond_load")
+
+    def wcl_precond_get(self):
+        import numpy as np
+
+        buf = np.zeros(2 * PTC_NWEIGHTS, dtype=np.float64)
+        _check(load_library().wcl_precond_get(self.handle, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_precond_get")
+        return buf.view(np.complex128)
+
+    def wcl_precond_apply(self, out_e, in_e, nrhs: int = 1, bf16: bool = False):
+        import torch
+
+        n = self.fermion_numel // 2 * nrhs
+        _check(load_library().wcl_precond_apply(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
+                                                _ptr(in_e, torch.complex128, n, "in_e"), nrhs, int(bf16)),
+               "wcl_precond_apply")
+
+    def wcl_precond_loss_grad(self, r_e, e_e, npairs: int):
+        import numpy as np
+        import torch
+
+        n = self.fermion_numel // 2 * npairs
+        loss = ctypes.c_double()
+        g = np.zeros(2 * PTC_NWEIGHTS, dtype=np.float64)
+        _check(load_library().wcl_precond_loss_grad(self.handle, _ptr(r_e, torch.complex128, n, "r_e"),
+                                                    _ptr(e_e, torch.complex128, n, "e_e"), npairs, ctypes.byref(loss),
+                                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_precond_loss_grad")
+        return loss.value, g.view(np.complex128)
+
+    def wcl_precond_train(self, r_e, e_e, npairs: int, params: wcl_train_params | None = None):
+        import numpy as np
+        import torch
+
+        if params is None:
+            params = wcl_train_params()
+            load_library().wcl_default_train_params(ctypes.byref(params))
+        n = self.fermion_numel // 2 * npairs
+        losses = np.zeros(params.epochs, dtype=np.float64)
+        _check(load_library().wcl_precond_train(self.handle, _ptr(r_e, torch.complex128, n, "r_e"),
+                                                _ptr(e_e, torch.complex128, n, "e_e"), npairs, ctypes.byref(params),
+                                                losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_precond_train")
+        return losses
+
     def wcl_set_profiling(self, enable: bool = True):
         _check(load_library().wcl_set_profiling(self.handle, int(enable)), "wcl_set_profiling")
 
@@ -218,6 +288,31 @@ class Context:
             self.wcl_destroy()
         except Exception:
             pass
+
+
+def wcl_default_train_params(**overrides) -> wcl_train_params:
+    p = wcl_train_params()
+    load_library().wcl_default_train_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def ptc_flatten(layers) -> "numpy.ndarray":
+    """Oracle-style list of (Cout, Cin, 9, 4, 4) complex arrays -> the flat weight vector."""
+    import numpy as np
+
+    return np.concatenate([np.asarray(w, dtype=np.complex128).ravel() for w in layers])
+
+
+def ptc_unflatten(flat):
+    """Flat weight vector -> list of (Cout, Cin, 9, 4, 4) arrays, channels 1, 4, 4, 4, 1."""
+    out, off = [], 0
+    for cin, cout in zip(PTC_CHANNELS[:-1], PTC_CHANNELS[1:]):
+        n = cout * cin * 9 * 16
+        out.append(flat[off:off + n].reshape(cout, cin, 9, 4, 4))
+        off += n
+    return out
 
 
 def _info_dict(i: wcl_solve_info) -> dict:
