@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--sloppy", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--delta", type=float, default=1e-3, help="reliable-update threshold")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="solve", choices=["solve", "mhat"],
+    ap.add_argument("--pairs", type=int, default=512, help="training pairs of --case compare")
+    ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
+    ap.add_argument("--case", default="solve", choices=["solve", "mhat", "compare"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures)")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
@@ -348,10 +350,117 @@ def run_mhat_case(args):
     return 0
 
 
+def run_compare_case(args):
+    """12 point sources on 32^3x64 solved four ways, each to a 1e-10 true residual:
+    plain FP32 single-RHS BiCGStab (12 sequential solves, FP64 restarts), the
+    batched 12-RHS mixed-precision BiCGStab, batched GCR(20), and batched
+    flexible GCR(20) with the PTC network trained on the GPU on pairs from
+    16^3x32 fields (kappa 0.124) and applied to a fresh 32^3x64 configuration."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    res = {"case": "compare", "workload": WORKLOAD}
+    # ---- training on 16^3x32, kappa 0.124 -----------------------------------
+    tdims, tkappa = (16, 16, 16, 32), 0.124
+    tctx = pkg.Context(tdims)
+    tctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(tdims, EPS, 100)).to(dev), tkappa, CSW)
+    rng = np.random.default_rng(101)
+    w0 = []
+    for cin, cout in zip(pkg.wcl.PTC_CHANNELS[:-1], pkg.wcl.PTC_CHANNELS[1:]):
+        w = 1e-3 * (rng.standard_normal((cout, cin, 9, 4, 4)) + 1j * rng.standard_normal((cout, cin, 9, 4, 4)))
+        w[0, 0, 0] += np.eye(4)
+        w0.append(w)
+    tctx.wcl_precond_load(pkg.ptc_flatten(w0))
+    # pairs (r, e) = (M_hat e, e): half Gaussian e, half partial BiCGStab solutions (low-mode rich)
+    n = args.pairs
+    vh = tdims[0] * tdims[1] * tdims[2] * tdims[3] // 2
+    es = torch.empty((n, vh * 12), dtype=torch.complex128, device=dev)
+    ng = n // 2
+    for k in range(0, ng, 64):
+        m = min(64, ng - k)
+        es[k:k + m] = torch.from_numpy(W.gaussian_fermion(tdims, 200 + k, nrhs=m)[:, 0].reshape(m, -1).copy()).to(dev)
+    k = ng
+    it = 4
+    while k < n:
+        m = min(12, n - k)
+        b = torch.from_numpy(W.z2_fermion(tdims, 300 + k, nrhs=m).reshape(m, -1)).to(dev)
+        x = torch.zeros_like(b)
+        tctx.wcl_invert(x, b, m, pkg.wcl_default_params(sloppy="f32", tol=1e-10, maxiter=it, check_every=2),
+                        check=False)
+        es[k:k + m] = x.reshape(m, 2, -1)[:, 0]
+        k += m
+        it = 4 + (it + 4) % 60
+    rs = torch.empty_like(es)
+    for k in range(0, n, 64):
+        m = min(64, n - k)
+        tctx.wcl_apply_Mpc(rs[k:k + m], es[k:k + m].contiguous(), "f64", nrhs=m)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = tctx.wcl_precond_train(rs, es, n, pkg.wcl_default_train_params(epochs=args.epochs, batch=8, lr=2e-3))
+    torch.cuda.synchronize()
+    res["training"] = {"lattice": "16x16x16x32", "kappa": tkappa, "pairs": n, "epochs": args.epochs,
+                       "seconds": time.perf_counter() - t0, "loss_per_epoch": [float(v) for v in losses]}
+    weights = tctx.wcl_precond_get()
+    tctx.close()
+    del es, rs
+
+    # ---- the four solves on 32^3x64 --------------------------------------------
+    gauge = W.gauge_links(DIMS, EPS, 7)  # a configuration the network never saw
+    src = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
+    ctx = pkg.Context(DIMS)
+    ctx.wcl_load_gauge(torch.from_numpy(gauge).to(dev), KAPPA, CSW)
+    del gauge
+    ctx.wcl_precond_load(weights)
+    b = torch.from_numpy(src).to(dev)
+    x = torch.zeros_like(b)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    def solve(params, nrhs=12):
+        return ctx.wcl_invert(x, b, nrhs, params)[1]
+
+    plain = pkg.wcl_default_params(sloppy="f32", tol=TOL, restart_on_update=1, delta_reliable=1e-5)
+    solve(pkg.wcl_default_params(sloppy="f32", tol=TOL))  # warm-up
+    sec, infos = timed(lambda: [ctx.wcl_invert(x[k:k + 1], b[k:k + 1], 1, plain)[1][0] for k in range(12)])
+    res["plain_f32_single_rhs"] = {"seconds": sec, "iters": [i["iters"] for i in infos],
+                                   "worst_true_residual": max(i["true_residual"] for i in infos)}
+    for name, prm in [("batched_bicgstab_f32", pkg.wcl_default_params(sloppy="f32", tol=TOL, delta_reliable=1e-3)),
+                      ("batched_bicgstab_f16", pkg.wcl_default_params(sloppy="f16", tol=TOL, delta_reliable=0.01)),
+                      ("batched_gcr20_f32", pkg.wcl_default_params(solver="gcr", sloppy="f32", tol=TOL,
+                                                                   delta_reliable=1e-3)),
+                      ("batched_fgcr20_learned_f32", pkg.wcl_default_params(solver="fgcr_learned", sloppy="f32",
+                                                                            tol=TOL, delta_reliable=1e-3))]:
+        sec, infos = timed(lambda: solve(prm))
+        res[name] = {"seconds": sec, "iters_per_rhs": float(np.mean([i["iters"] for i in infos])),
+                     "worst_true_residual": max(i["true_residual"] for i in infos),
+                     "reliable_updates": float(np.mean([i["reliable_updates"] for i in infos]))}
+    base = res["plain_f32_single_rhs"]["seconds"]
+    for k2 in list(res):
+        if isinstance(res[k2], dict) and "seconds" in res[k2] and k2 != "training":
+            res[k2]["speedup_vs_plain"] = base / res[k2]["seconds"]
+    print(json.dumps(res))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.case == "mhat":
         return run_mhat_case(args)
+    if args.case == "compare":
+        return run_compare_case(args)
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores only; other ranks exit without work
         return run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
