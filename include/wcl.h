@@ -199,6 +199,16 @@ wcl_status wcl_precond_loss_grad(wcl_ctx* ctx, const void* d_r_e, const void* d_
 wcl_status wcl_precond_train(wcl_ctx* ctx, const void* d_r_e, const void* d_e_e, int npairs,
                              const wcl_train_params* params, double* h_loss_per_epoch);
 
+/* Options of a context (wcl_set_option). */
+typedef enum {
+  WCL_OPT_TENSOR_CORES = 1 /* 1: 16-bit multi-RHS dslash (4..16 RHS) with the link and clover
+                              multiplies on the tensor cores (mma.sync, FP32 accumulation);
+                              0 (default): the per-thread kernel, faster with this field layout */
+} wcl_option;
+
+/* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */
+wcl_status wcl_set_option(wcl_ctx* ctx, int option, int value);
+
 /* Counters for measurement. */
 typedef struct {
   long long kernel_launches; /* every kernel of this library launched on ctx (graph replays included) */

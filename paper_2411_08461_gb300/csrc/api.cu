@@ -389,6 +389,15 @@ wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, co
   return leave(ctxs[0], s);
 }
 
+wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
+  if (!c) return WCL_ERR_INVALID_ARG;
+  switch (option) {
+    case WCL_OPT_TENSOR_CORES: c->tensor_cores = value != 0; return WCL_OK;
+  }
+  set_error("wcl_set_option: unknown option %d", option);
+  return WCL_ERR_INVALID_ARG;
+}
+
 wcl_status wcl_set_profiling(wcl_ctx* c, int enable) {
   if (!c) return WCL_ERR_INVALID_ARG;
   c->profiling = enable != 0;

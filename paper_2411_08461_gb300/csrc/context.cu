@@ -111,8 +111,13 @@ wcl_status dslash(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const F
   return dslash_ex(ctxs, prec, nrhs, out, in, x, nullptr, out_parity, dagger, post, pre, alpha, beta, active);
 }
 
+bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode) {
+  return c->tensor_cores && prec == F16 && nrhs >= 4 && nrhs <= 16 &&
+         (mode == MODE_POST || mode == (MODE_XPAY | MODE_PRE));
+}
+
 int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
-  const int block = ctxs[0]->dslash_block[prec];
+  const int block = (prec == F16 && ctxs[0]->tensor_cores) ? tc_tile_sites() : ctxs[0]->dslash_block[prec];
   long m = 1;
   for (auto* c : ctxs) m = std::max(m, (c->lat.vh + block - 1) / block);
   return (int)m;
@@ -162,17 +167,30 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   if (x) mode |= MODE_XPAY;
   if (x && pre) mode |= MODE_PRE;
   if (out2) mode |= MODE_RECON;
+  const bool tc = use_tc(c0, prec, nrhs, mode);
+  if (tc) {
+    a.b = make_batch(ctxs, 1, tc_tile_sites(), 0);  // one CTA covers all right-hand sides of its sites
+    for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
+    a.nrhs_tc = nrhs;
+  }
   if (epi) mode |= epi->kind << 5;
   wcl_ctx::Timed* t = prof_begin(c0);
   cudaError_t e;
-  switch (prec) {
+  if (tc) {
+    e = launch_dslash_tc(prec, a, dagger, mode, c0->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core dslash launch");
+    count_launch(c0, true);
+    if (epi && epi->kind != EPI_NONE) count_launch(c0);
+  } else switch (prec) {
     case F64: e = launch_dslash<F64>(a, dagger, mode, block, c0->stream); break;
     case F32: e = launch_dslash<F32>(a, dagger, mode, block, c0->stream); break;
     case F16: e = launch_dslash<F16>(a, dagger, mode, block, c0->stream); break;
     default: e = launch_dslash<BF16>(a, dagger, mode, block, c0->stream); break;
   }
-  if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
-  count_launch(c0, true);
+  if (!tc) {
+    if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
+    count_launch(c0, true);
+  }
   if (t) {
     cudaEventRecord(t->b, c0->stream);
     double sp, lk, cl;

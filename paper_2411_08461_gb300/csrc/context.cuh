@@ -52,6 +52,7 @@ struct wcl_ctx {
 
   // launch shapes (picked by the tuner on first use)
   int dslash_block[4] = {128, 128, 128, 128};
+  bool tensor_cores = false;  // multi-RHS 16-bit dslash on mma.sync (WCL_OPT_TENSOR_CORES)
   int blas_block = 256;
 };
 
@@ -136,6 +137,11 @@ wcl_status apply_mhat(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, con
 // precision conversion of a parity field
 wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrhs, const FieldRef& out,
                    const FieldRef& in, const int* active);
+
+// tensor-core multi-RHS dslash (dslash_tc.cu): 16-bit storage, 4 <= nrhs <= 16
+cudaError_t launch_dslash_tc(int prec, const DslashArgs& a, bool dagger, int mode, cudaStream_t st);
+int tc_tile_sites();
+bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
 
 // per-precision instantiations (defined in dslash_<prec>.cu)
 template <int P>

@@ -53,6 +53,7 @@ struct DslashArgs {
   unsigned* counters; // [slot], zero between launches
   Scalars* sc;
   int maxch;
+  int nrhs_tc;        // tensor-core kernel: right-hand sides per lattice (one CTA covers all)
 };
 
 template <int EPI>

@@ -23,6 +23,7 @@ STATUS_NAMES = {
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3}
 PTC_NWEIGHTS = 5760
+WCL_OPT_TENSOR_CORES = 1
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 
@@ -75,6 +76,7 @@ SIGNATURES = {
                                         ctypes.c_int, ctypes.POINTER(wcl_solve_params),
                                         ctypes.POINTER(wcl_solve_info)]),
     "wcl_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wcl_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "wcl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(wcl_stats), ctypes.c_int]),
     "wcl_apply_Mpc_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "wcl_default_train_params": (None, [ctypes.POINTER(wcl_train_params)]),
@@ -267,6 +269,9 @@ class Context:
                                                 losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "wcl_precond_train")
         return losses
+
+    def wcl_set_option(self, option: int, value: int):
+        _check(load_library().wcl_set_option(self.handle, int(option), int(value)), "wcl_set_option")
 
     def wcl_set_profiling(self, enable: bool = True):
         _check(load_library().wcl_set_profiling(self.handle, int(enable)), "wcl_set_profiling")

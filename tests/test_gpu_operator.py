@@ -91,3 +91,38 @@ def test_gamma5_hermiticity_on_gpu(pkg):
     rhs = np.vdot(g5 * host(mphi), psi)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
     ctx.close()
+
+
+@pytest.mark.parametrize("tensor_cores", [1, 0])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((4, 4, 4, 4), 5), ((8, 4, 4, 6), 16)])
+def test_apply_Mpc_multi_rhs_f16(pkg, dims, nrhs, dagger, tensor_cores):
+    """12-RHS 16-bit Schur operator: tensor-core (mma.sync f16, FP32 accumulate) and per-thread kernels."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_TENSOR_CORES
+
+    ctx, op, _ = _setup(pkg, dims, seed=13)
+    ctx.wcl_set_option(WCL_OPT_TENSOR_CORES, tensor_cores)
+    psi = W.gaussian_fermion(dims, 14, nrhs=nrhs)[:, 0].copy()
+    psi[1] *= 1e-7  # very different magnitudes per right-hand side
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), "f16", nrhs=nrhs, dagger=dagger)
+    got = host(out)
+    for k in range(nrhs):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL["f16"], k
+    ctx.close()
+
+
+def test_tensor_core_and_per_thread_kernels_agree(pkg):
+    from paper_2411_08461_gb300.wcl import WCL_OPT_TENSOR_CORES
+
+    dims = (8, 8, 8, 16)
+    ctx, _, _ = _setup(pkg, dims, seed=15)
+    psi = cuda(W.gaussian_fermion(dims, 16, nrhs=12)[:, 0].copy())
+    outs = []
+    for tc in (1, 0):
+        ctx.wcl_set_option(WCL_OPT_TENSOR_CORES, tc)
+        o = cuda(np.zeros(psi.shape, dtype=np.complex128))
+        ctx.wcl_apply_Mpc(o, psi, "f16", nrhs=12)
+        outs.append(host(o))
+    assert relerr(outs[0], outs[1]) <= 5e-3
+    ctx.close()

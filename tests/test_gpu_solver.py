@@ -142,3 +142,22 @@ def test_errors(pkg):
     st, _ = ctx.wcl_invert(x, b, 1, pkg.wcl_default_params(solver="fgcr_learned"), check=False)
     assert st == 10
     ctx.close()
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
+def test_twelve_rhs_f16_tensor_core_solve(pkg, solver):
+    """FP16 inner solver with the tensor-core dslash and its fused reductions reaches 1e-10."""
+    dims = (8, 8, 8, 16)
+    gauge = W.gauge_links(dims, 0.3, 5)
+    ctx = pkg.Context(dims)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_TENSOR_CORES, 1)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    b = W.z2_fermion(dims, 6, nrhs=12)
+    x = cuda(np.zeros_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 12, pkg.wcl_default_params(solver=solver, sloppy="f16", tol=1e-10,
+                                                                   delta_reliable=0.01))
+    op = dirac.from_qdp_problem(gauge, dims, 0.1235, 1.0)
+    xh = host(x)
+    for k in range(12):
+        assert _oracle_true_residual(op, xh[k], b[k]) <= 1e-10, (k, info[k])
+    ctx.close()
