@@ -53,8 +53,10 @@ def parse():
                     help="mhat: only apply the Schur operator (the small case used for ncu captures)")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
-    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"], help="precision of --case mhat")
-    ap.add_argument("--tensor-cores", type=int, default=1, help="--case mhat: 16-bit multi-RHS kernel on tensor cores")
+    ap.add_argument("--prec", default="f32", choices=["f64", "df64", "f32", "f16", "bf16"], help="precision of --case mhat")
+    ap.add_argument("--tensor-cores", type=int, default=0, help="--case mhat: 16-bit multi-RHS kernel on tensor cores")
+    ap.add_argument("--shared-links", type=int, default=1,
+                    help="--case mhat: multi-RHS kernel with links and clover staged in shared memory")
     return ap.parse_args()
 
 
@@ -331,6 +333,7 @@ def run_mhat_case(args):
     dims = tuple(int(v) for v in args.lattice.split(","))
     ctx = pkg.Context(dims)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_TENSOR_CORES, args.tensor_cores)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_SHARED_LINKS, args.shared_links)
     ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, SEED)).cuda(), KAPPA, CSW)
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     psi = torch.from_numpy(W.gaussian_fermion(dims, 1, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(-1)
@@ -346,7 +349,7 @@ def run_mhat_case(args):
     peak, kind = measured_peaks()
     gbs = st["dslash_bytes"] / (st["dslash_ms"] * 1e-3) / 1e9
     print(json.dumps({"case": "mhat", "lattice": dims, "nrhs": args.nrhs, "prec": args.prec,
-                      "tensor_cores": args.tensor_cores,
+                      "tensor_cores": args.tensor_cores, "shared_links": args.shared_links,
                       "dslash_launches": st["dslash_timed"], "avg_launch_ms": st["dslash_ms"] / st["dslash_timed"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind}))
     ctx.close()

@@ -71,7 +71,15 @@ typedef enum {
   WCL_ERR_NO_PRECOND = 10   /* learned solver requested without weights */
 } wcl_status;
 
-typedef enum { WCL_F64 = 0, WCL_F32 = 1, WCL_F16 = 2, WCL_BF16 = 3 } wcl_prec;
+typedef enum {
+  WCL_F64 = 0,
+  WCL_F32 = 1,
+  WCL_F16 = 2,   /* FP16 storage with per-site norms, FP32 arithmetic */
+  WCL_BF16 = 3,  /* BF16 storage with per-site norms, FP32 arithmetic */
+  WCL_DF64 = 4   /* FP64 fields, double-float arithmetic (two FP32, ~48-bit significand);
+                    wcl_apply_D / wcl_apply_Mpc only.  The solvers use it for residual
+                    replacements in the middle of a solve; every reported residual is FP64. */
+} wcl_prec;
 
 typedef enum {
   WCL_BICGSTAB = 0,      /* BiCGStab on M_hat (Sec. II.E: default for clover) */
@@ -204,6 +212,10 @@ typedef enum {
   WCL_OPT_TENSOR_CORES = 1 /* 1: 16-bit multi-RHS dslash (4..16 RHS) with the link and clover
                               multiplies on the tensor cores (mma.sync, FP32 accumulation);
                               0 (default): the per-thread kernel, faster with this field layout */
+  ,
+  WCL_OPT_SHARED_LINKS = 2 /* 1 (default): multi-RHS dslash (4..16 RHS, Schur operator) stages the
+                              links and clover of a 16-site tile in shared memory once for all RHS;
+                              0: one thread per (site, RHS) reading its own links and clover */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

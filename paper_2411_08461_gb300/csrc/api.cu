@@ -42,6 +42,7 @@ wcl_status enter(wcl_ctx* c) { return wcl_enter(c); }
 wcl_status leave(wcl_ctx* c, wcl_status s) { return wcl_leave(c, s); }
 
 bool valid_prec(int p) { return p >= WCL_F64 && p <= WCL_BF16; }
+bool valid_apply_prec(int p) { return p >= WCL_F64 && p <= WCL_DF64; }
 
 wcl_status alloc_lattice(wcl_ctx* c) {
   LatticeDevice& L = c->lat;
@@ -220,7 +221,7 @@ wcl_status wcl_load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, double 
 }
 
 wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec, int nrhs) {
-  if (!c || !d_out || !d_in || nrhs < 1 || nrhs > 64 || !valid_prec(prec)) {
+  if (!c || !d_out || !d_in || nrhs < 1 || nrhs > 64 || !valid_apply_prec(prec)) {
     set_error("wcl_apply_D: invalid argument");
     return WCL_ERR_INVALID_ARG;
   }
@@ -241,7 +242,7 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
   WCL_CUDA(import_fermion(L, d_in, rs, L.vh * 12, nrhs, io.ptr[0], nullptr, c->stream));
   count_launch(c);
   count_launch(c);
-  if (prec == WCL_F64) {
+  if (prec == WCL_F64 || prec == WCL_DF64) {
     pe = ie, po = io, qe = oe, qo = oo;
   } else {
     WCL_CHECK(ws_field(v, "D_pin_e", prec, nrhs, &pe));
@@ -254,7 +255,7 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
   // out_p = A_pp in_p - kappa D_{p,1-p} in_{1-p}
   WCL_CHECK(dslash(v, prec, nrhs, qe, po, &pe, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
   WCL_CHECK(dslash(v, prec, nrhs, qo, pe, &po, 1, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
-  if (prec != WCL_F64) {
+  if (prec != WCL_F64 && prec != WCL_DF64) {
     WCL_CHECK(convert(v, F64, prec, nrhs, oe, qe, nullptr));
     WCL_CHECK(convert(v, F64, prec, nrhs, oo, qo, nullptr));
   }
@@ -268,7 +269,7 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
 }
 
 wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec prec, int nrhs, int dagger) {
-  if (!c || !d_out_e || !d_in_e || nrhs < 1 || nrhs > 64 || !valid_prec(prec)) {
+  if (!c || !d_out_e || !d_in_e || nrhs < 1 || nrhs > 64 || !valid_apply_prec(prec)) {
     set_error("wcl_apply_Mpc: invalid argument");
     return WCL_ERR_INVALID_ARG;
   }
@@ -280,13 +281,14 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
   std::vector<wcl_ctx*> v{c};
   const LatticeDevice& L = c->lat;
   FieldRef ie, oe, pe, qe, tmp;
+  const bool fp64_fields = prec == WCL_F64 || prec == WCL_DF64;
   WCL_CHECK(ws_field(v, "M_in", F64, nrhs, &ie));
   WCL_CHECK(ws_field(v, "M_out", F64, nrhs, &oe));
-  WCL_CHECK(ws_field(v, "M_tmp", prec, nrhs, &tmp));
+  WCL_CHECK(ws_field(v, "M_tmp", fp64_fields ? F64 : prec, nrhs, &tmp));
   const long rs = L.vh * 12;
   WCL_CUDA(import_fermion(L, d_in_e, rs, 0, nrhs, ie.ptr[0], nullptr, c->stream));
   count_launch(c);
-  if (prec == WCL_F64) {
+  if (fp64_fields) {
     pe = ie, qe = oe;
   } else {
     WCL_CHECK(ws_field(v, "M_pin", prec, nrhs, &pe));
@@ -294,7 +296,7 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
     WCL_CHECK(convert(v, prec, F64, nrhs, pe, ie, nullptr));
   }
   WCL_CHECK(apply_mhat(v, prec, nrhs, qe, pe, tmp, dagger != 0, nullptr));
-  if (prec != WCL_F64) WCL_CHECK(convert(v, F64, prec, nrhs, oe, qe, nullptr));
+  if (!fp64_fields) WCL_CHECK(convert(v, F64, prec, nrhs, oe, qe, nullptr));
   WCL_CUDA(export_fermion(L, oe.ptr[0], nrhs, d_out_e, rs, 0, c->stream));
   count_launch(c);
   wcl_status s = leave(c, WCL_OK);
@@ -393,6 +395,7 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
   if (!c) return WCL_ERR_INVALID_ARG;
   switch (option) {
     case WCL_OPT_TENSOR_CORES: c->tensor_cores = value != 0; return WCL_OK;
+    case WCL_OPT_SHARED_LINKS: c->shared_links = value != 0; return WCL_OK;
   }
   set_error("wcl_set_option: unknown option %d", option);
   return WCL_ERR_INVALID_ARG;

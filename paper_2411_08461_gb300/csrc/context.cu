@@ -87,7 +87,8 @@ Batch make_batch(const std::vector<wcl_ctx*>& ctxs, int nrhs, int block, int cap
 
 static void spinor_site_bytes(int prec, double& sp, double& link, double& clov) {
   switch (prec) {
-    case F64: sp = 192; link = 144; clov = 576; break;
+    case F64:
+    case DF64: sp = 192; link = 144; clov = 576; break;
     case F32: sp = 96; link = 48; clov = 288; break;
     default: sp = 52; link = 24; clov = 148; break;
   }
@@ -116,8 +117,14 @@ bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode) {
          (mode == MODE_POST || mode == (MODE_XPAY | MODE_PRE));
 }
 
+bool use_mrhs(const wcl_ctx* c, int prec, int nrhs, int mode) {
+  return c->shared_links && prec != DF64 && nrhs >= 4 && nrhs * MR_SITES <= 256 &&
+         (mode == MODE_POST || mode == (MODE_XPAY | MODE_PRE));
+}
+
 int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
-  const int block = (prec == F16 && ctxs[0]->tensor_cores) ? tc_tile_sites() : ctxs[0]->dslash_block[prec];
+  // smallest site tile any dslash kernel may use, so that the partials fit every variant
+  const int block = std::min(ctxs[0]->dslash_block[prec], std::min(tc_tile_sites(), MR_SITES));
   long m = 1;
   for (auto* c : ctxs) m = std::max(m, (c->lat.vh + block - 1) / block);
   return (int)m;
@@ -127,7 +134,8 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
                      const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
                      CloverSel pre, Coef alpha, Coef beta, const int* active, const EpiSpec* epi) {
   wcl_ctx* c0 = ctxs[0];
-  const int block = c0->dslash_block[prec];
+  const int dp = prec == DF64 ? F64 : prec;  // data precision (double-float reads the FP64 fields)
+  const int block = c0->dslash_block[dp];
   DslashArgs a;
   memset(&a, 0, sizeof a);
   a.b = make_batch(ctxs, nrhs, block, 0);
@@ -147,16 +155,16 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   double sites = 0;
   for (size_t l = 0; l < ctxs.size(); l++) {
     const LatticeDevice& L = ctxs[l]->lat;
-    a.gauge[l][0] = L.gauge[prec][0];
-    a.gauge[l][1] = L.gauge[prec][1];
+    a.gauge[l][0] = L.gauge[dp][0];
+    a.gauge[l][1] = L.gauge[dp][1];
     const int p = out_parity;
     if (post) {
-      a.cpost[l] = post == CL_A ? L.clov[prec][p] : L.clovinv[prec][p];
-      a.cpost_norm[l] = post == CL_A ? L.clov_norm[prec * 2 + p] : L.clovinv_norm[prec * 2 + p];
+      a.cpost[l] = post == CL_A ? L.clov[dp][p] : L.clovinv[dp][p];
+      a.cpost_norm[l] = post == CL_A ? L.clov_norm[dp * 2 + p] : L.clovinv_norm[dp * 2 + p];
     }
     if (pre) {
-      a.cpre[l] = pre == CL_A ? L.clov[prec][p] : L.clovinv[prec][p];
-      a.cpre_norm[l] = pre == CL_A ? L.clov_norm[prec * 2 + p] : L.clovinv_norm[prec * 2 + p];
+      a.cpre[l] = pre == CL_A ? L.clov[dp][p] : L.clovinv[dp][p];
+      a.cpre_norm[l] = pre == CL_A ? L.clov_norm[dp * 2 + p] : L.clovinv_norm[dp * 2 + p];
     }
     a.alpha[l] = coef_value(alpha, L.kappa);
     a.beta[l] = coef_value(beta, L.kappa);
@@ -168,6 +176,12 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   if (x && pre) mode |= MODE_PRE;
   if (out2) mode |= MODE_RECON;
   const bool tc = use_tc(c0, prec, nrhs, mode);
+  const bool mr = !tc && use_mrhs(c0, prec, nrhs, mode);
+  if (mr) {
+    a.b = make_batch(ctxs, 1, MR_SITES, 0);  // one CTA covers all right-hand sides of its sites
+    for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
+    a.nrhs_tc = nrhs;
+  }
   if (tc) {
     a.b = make_batch(ctxs, 1, tc_tile_sites(), 0);  // one CTA covers all right-hand sides of its sites
     for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
@@ -181,13 +195,24 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core dslash launch");
     count_launch(c0, true);
     if (epi && epi->kind != EPI_NONE) count_launch(c0);
+  } else if (mr) {
+    switch (prec) {
+      case F64: e = launch_dslash_mrhs<F64>(a, dagger, mode, c0->stream); break;
+      case F32: e = launch_dslash_mrhs<F32>(a, dagger, mode, c0->stream); break;
+      case F16: e = launch_dslash_mrhs<F16>(a, dagger, mode, c0->stream); break;
+      default: e = launch_dslash_mrhs<BF16>(a, dagger, mode, c0->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "multi-RHS dslash launch");
+    count_launch(c0, true);
+    if (epi && epi->kind != EPI_NONE) count_launch(c0);
   } else switch (prec) {
     case F64: e = launch_dslash<F64>(a, dagger, mode, block, c0->stream); break;
+    case DF64: e = launch_dslash<DF64>(a, dagger, mode, block, c0->stream); break;
     case F32: e = launch_dslash<F32>(a, dagger, mode, block, c0->stream); break;
     case F16: e = launch_dslash<F16>(a, dagger, mode, block, c0->stream); break;
     default: e = launch_dslash<BF16>(a, dagger, mode, block, c0->stream); break;
   }
-  if (!tc) {
+  if (!tc && !mr) {
     if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
     count_launch(c0, true);
   }
@@ -217,14 +242,16 @@ wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, c
   a.out = out;
   a.x = x;
   a.active = active;
+  const int dp = prec == DF64 ? F64 : prec;
   for (size_t l = 0; l < ctxs.size(); l++) {
     const LatticeDevice& L = ctxs[l]->lat;
-    a.c[l] = which == CL_A ? L.clov[prec][parity] : L.clovinv[prec][parity];
-    a.c_norm[l] = which == CL_A ? L.clov_norm[prec * 2 + parity] : L.clovinv_norm[prec * 2 + parity];
+    a.c[l] = which == CL_A ? L.clov[dp][parity] : L.clovinv[dp][parity];
+    a.c_norm[l] = which == CL_A ? L.clov_norm[dp * 2 + parity] : L.clovinv_norm[dp * 2 + parity];
   }
   cudaError_t e;
   switch (prec) {
     case F64: e = launch_clover<F64>(a, block, c0->stream); break;
+    case DF64: e = launch_clover<DF64>(a, block, c0->stream); break;
     case F32: e = launch_clover<F32>(a, block, c0->stream); break;
     case F16: e = launch_clover<F16>(a, block, c0->stream); break;
     default: e = launch_clover<BF16>(a, block, c0->stream); break;

@@ -53,6 +53,7 @@ struct wcl_ctx {
   // launch shapes (picked by the tuner on first use)
   int dslash_block[4] = {128, 128, 128, 128};
   bool tensor_cores = false;  // multi-RHS 16-bit dslash on mma.sync (WCL_OPT_TENSOR_CORES)
+  bool shared_links = true;   // multi-RHS dslash with links/clover staged in shared memory
   int blas_block = 256;
 };
 
@@ -142,6 +143,7 @@ wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrh
 cudaError_t launch_dslash_tc(int prec, const DslashArgs& a, bool dagger, int mode, cudaStream_t st);
 int tc_tile_sites();
 bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
+bool use_mrhs(const wcl_ctx* c, int prec, int nrhs, int mode);
 
 // per-precision instantiations (defined in dslash_<prec>.cu)
 template <int P>

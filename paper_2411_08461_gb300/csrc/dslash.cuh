@@ -288,11 +288,352 @@ __global__ void __launch_bounds__(256) clover_kernel(const __grid_constant__ Clo
   SpinorIO<P>::store(y, rhs_ptr_w<P>(a.out, s.l, s.rhs, g.stride), rhs_norm(a.out, s.l, s.rhs, g.stride), g.stride, i);
 }
 
+// ---------------------------------------------------------------------------
+// Multi-RHS kernel: a CTA covers MR_SITES consecutive output sites and every
+// right-hand side.  Links and clover of the tile are read from memory once,
+// unpacked (12-real reconstruction, 16-bit scaling) into shared memory, and
+// reused by all RHS; each thread then computes one (site, rhs) pair.  Threads
+// of one RHS form a half warp.  Fused reductions write one partial per (RHS,
+// CTA) and are finalised by tc_epi_finalize_kernel.
+constexpr int MR_SITES = 16;
+
+// Unpack chunk k of the packed clover term of site i into reals r[0..n) (n per chunk:
+// 2 for FP64, 4 for FP32, 8 for the 16-bit formats, which carry one scale per site).
+template <int P>
+struct CloverChunk;
+template <>
+struct CloverChunk<F64> {
+  static constexpr int NCH = 36, PER = 2;
+  __device__ static void load(double r[2], const void* base, const float*, long stride, long i, int k) {
+    const double2 v = ldg(static_cast<const double2*>(base) + k * stride + i);
+    r[0] = v.x;
+    r[1] = v.y;
+  }
+};
+template <>
+struct CloverChunk<F32> {
+  static constexpr int NCH = 18, PER = 4;
+  __device__ static void load(float r[4], const void* base, const float*, long stride, long i, int k) {
+    const float4 v = ldg(static_cast<const float4*>(base) + k * stride + i);
+    r[0] = v.x;
+    r[1] = v.y;
+    r[2] = v.z;
+    r[3] = v.w;
+  }
+};
+template <int P>
+struct CloverChunk16 {
+  static constexpr int NCH = 9, PER = 8;
+  __device__ static void load(float r[8], const void* base, const float* norm, long stride, long i, int k) {
+    const uint4 q = ldg(static_cast<const uint4*>(base) + k * stride + i);
+    const float n = __ldg(norm + i);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const float2 f = unpack2<P>(w[j]);
+      r[2 * j] = f.x * n;
+      r[2 * j + 1] = f.y * n;
+    }
+  }
+};
+template <>
+struct CloverChunk<F16> : CloverChunk16<F16> {};
+template <>
+struct CloverChunk<BF16> : CloverChunk16<BF16> {};
+
+template <typename R>
+__device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[12], const R (*C)[MR_SITES], int ls) {
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    R d[6];
+    cpx<R> L[15];
+#pragma unroll
+    for (int k = 0; k < 6; k++) d[k] = C[36 * b + k][ls];
+#pragma unroll
+    for (int k = 0; k < 15; k++) L[k] = {C[36 * b + 6 + 2 * k][ls], C[36 * b + 7 + 2 * k][ls]};
+    hermitian6_apply(y + 6 * b, d, L, x + 6 * b);
+  }
+}
+
+template <int P, int MU, bool DAG>
+__device__ __forceinline__ void hop_dir_smem(cpx<typename Traits<P>::R> acc[12], const void* in, const float* in_norm,
+                                             long stride, long jf, long jb, const typename Traits<P>::R (*U)[18][MR_SITES],
+                                             int ls, typename Traits<P>::R sf, typename Traits<P>::R sb) {
+  using R = typename Traits<P>::R;
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr int SB = -SF;
+  cpx<R> psi[12], h[6], uh[6], u[3][3];
+  SpinorIO<P>::load(psi, in, in_norm, stride, jf);
+#pragma unroll
+  for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {U[2 * MU][2 * k][ls], U[2 * MU][2 * k + 1][ls]};
+  project<MU, SF>(psi, h);
+  link_mul<false>(u, h, uh, sf);
+  reconstruct_acc<MU, SF>(acc, uh);
+  SpinorIO<P>::load(psi, in, in_norm, stride, jb);
+#pragma unroll
+  for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {U[2 * MU + 1][2 * k][ls], U[2 * MU + 1][2 * k + 1][ls]};
+  project<MU, SB>(psi, h);
+  link_mul<true>(u, h, uh, sb);
+  reconstruct_acc<MU, SB>(acc, uh);
+}
+
+struct SiteNbr {
+  long jf[4], jb[4];
+  int t;
+};
+__device__ __forceinline__ SiteNbr site_neighbours(const LatGeom& g, int p, long i) {
+  SiteNbr n;
+  const int lxh = g.lxh, Lx = g.dims[0], Ly = g.dims[1], Lz = g.dims[2], Lt = g.dims[3];
+  const int xh = (int)(i % lxh);
+  int rem = (int)(i / lxh);
+  const int y = rem % Ly;
+  rem /= Ly;
+  const int z = rem % Lz;
+  const int t = rem / Lz;
+  const int x = 2 * xh + ((p + y + z + t) & 1);
+  const long row = i - xh;
+  const long plane = (long)lxh * Ly, vol3 = plane * Lz;
+  n.jf[0] = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
+  n.jb[0] = row + ((x == 0 ? Lx - 1 : x - 1) >> 1);
+  n.jf[1] = (y + 1 == Ly) ? i - (long)(Ly - 1) * lxh : i + lxh;
+  n.jb[1] = (y == 0) ? i + (long)(Ly - 1) * lxh : i - lxh;
+  n.jf[2] = (z + 1 == Lz) ? i - (long)(Lz - 1) * plane : i + plane;
+  n.jb[2] = (z == 0) ? i + (long)(Lz - 1) * plane : i - plane;
+  n.jf[3] = (t + 1 == Lt) ? i - (long)(Lt - 1) * vol3 : i + vol3;
+  n.jb[3] = (t == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3;
+  n.t = t;
+  return n;
+}
+
+template <int P, bool DAG, int MODE, int EPI>
+__global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
+  using R = typename Traits<P>::R;
+  constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
+  __shared__ R Us[8][18][MR_SITES];
+  __shared__ R Cs[CLOV ? 72 : 1][MR_SITES];
+  const Slice s = find_slice(a.b, blockIdx.x);  // one slice per lattice
+  const LatGeom& g = a.b.lat[s.l];
+  const int nrhs = a.nrhs_tc;
+  const int slot0 = s.l * nrhs;
+  const int p = a.out_parity;
+  const long stride = g.stride;
+  const long site0 = (long)s.chunk * MR_SITES;
+
+  // phase 1: links (fwd at the site, bwd at the neighbour) and clover of the tile
+  for (int e = threadIdx.x; e < 8 * MR_SITES; e += blockDim.x) {
+    const int ls = e % MR_SITES, d = e / MR_SITES, mu = d >> 1;
+    const long i = site0 + ls;
+    cpx<R> u[3][3];
+    if (i < g.vh) {
+      if (d & 1) {
+        const SiteNbr n = site_neighbours(g, p, i);
+        LinkIO<P>::load(u, a.gauge[s.l][1 - p], stride, n.jb[mu], mu);
+      } else {
+        LinkIO<P>::load(u, a.gauge[s.l][p], stride, i, mu);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {R(0), R(0)};
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      Us[d][2 * k][ls] = u[k / 3][k % 3].re;
+      Us[d][2 * k + 1][ls] = u[k / 3][k % 3].im;
+    }
+  }
+  if (CLOV) {
+    using CC = CloverChunk<P>;
+    const void* cb = (MODE & MODE_POST) ? a.cpost[s.l] : a.cpre[s.l];
+    const float* cn = (MODE & MODE_POST) ? a.cpost_norm[s.l] : a.cpre_norm[s.l];
+    for (int e = threadIdx.x; e < CC::NCH * MR_SITES; e += blockDim.x) {
+      const int ls = e % MR_SITES, k = e / MR_SITES;
+      const long i = site0 + ls;
+      R r[CC::PER];
+      if (i < g.vh) {
+        CC::load(r, cb, cn, stride, i, k);
+      } else {
+#pragma unroll
+        for (int j = 0; j < CC::PER; j++) r[j] = R(0);
+      }
+#pragma unroll
+      for (int j = 0; j < CC::PER; j++) Cs[CLOV ? CC::PER * k + j : 0][ls] = r[j];
+    }
+  }
+  __syncthreads();
+
+  // phase 2: thread = (site ls, rhs)
+  const int ls = threadIdx.x & (MR_SITES - 1), rhs = threadIdx.x / MR_SITES;
+  const long i = site0 + ls;
+  double red[3] = {0.0, 0.0, 0.0};
+  const bool valid = rhs < nrhs && i < g.vh && (!a.active || a.active[slot0 + rhs]);
+  if (valid) {
+    const SiteNbr n = site_neighbours(g, p, i);
+    const void* in = rhs_ptr<P>(a.in, s.l, rhs, stride);
+    const float* in_norm = rhs_norm(a.in, s.l, rhs, stride);
+    cpx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
+    hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, n.jf[0], n.jb[0], Us, ls, R(1), R(1));
+    hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, n.jf[1], n.jb[1], Us, ls, R(1), R(1));
+    hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, n.jf[2], n.jb[2], Us, ls, R(1), R(1));
+    const R sf = (n.t + 1 == g.dims[3]) ? R(g.tb) : R(1);
+    const R sb = (n.t == 0) ? R(g.tb) : R(1);
+    hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, n.jf[3], n.jb[3], Us, ls, sf, sb);
+    const R alpha = R(a.alpha[s.l]);
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
+    if (MODE & MODE_XPAY) {
+      cpx<R> xv[12];
+      SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, rhs, stride), rhs_norm(a.x, s.l, rhs, stride), stride, i);
+      const R beta = R(a.beta[s.l]);
+      if (MODE & MODE_PRE) {
+        cpx<R> cx[12];
+        clover_apply_smem(cx, xv, Cs, ls);
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * cx[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
+      }
+      if (EPI == EPI_ALPHA) {
+        cpx<R> fv[12];
+        SpinorIO<P>::load(fv, rhs_ptr<P>(a.f, s.l, rhs, stride), rhs_norm(a.f, s.l, rhs, stride), stride, i);
+        dot_acc(red, fv, acc);
+      } else if (EPI == EPI_OMEGA) {
+        dot_acc(red, acc, xv);
+        red[2] += norm_site(acc);
+      } else if (EPI == EPI_CGALPHA || EPI == EPI_CGZ) {
+        red[0] += norm_site(acc);
+      }
+    }
+    if (MODE & MODE_POST) {
+      cpx<R> y2[12];
+      clover_apply_smem(y2, acc, Cs, ls);
+      SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
+    } else {
+      SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
+    }
+  }
+  if constexpr (EPI != EPI_NONE) {
+    // the MR_SITES threads of one rhs are one half warp
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+      for (int o = MR_SITES / 2; o; o >>= 1) red[k] += __shfl_xor_sync(0xffffffffu, red[k], o);
+    if (ls == 0 && rhs < nrhs) {
+      double* dst = a.partials + ((size_t)(slot0 + rhs) * a.maxch + s.chunk) * 3;
+      dst[0] = red[0];
+      dst[1] = red[1];
+      dst[2] = red[2];
+    }
+  }
+}
+
+// sums the per-CTA partials of every slot of a multi-RHS launch and runs the finaliser
+struct TcChunks {
+  int nch[MAXLAT];  // CTAs (partials) per lattice
+  int nrhs;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(256) tc_epi_finalize_kernel(const double* __restrict__ partials, int maxch,
+                                                              TcChunks ch, const int* __restrict__ active,
+                                                              Scalars* sc) {
+  const int slot = blockIdx.x;
+  if (active && !active[slot]) return;
+  const int n = ch.nch[slot / ch.nrhs];
+  double acc[3] = {0, 0, 0};
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    for (int k = 0; k < 3; k++) acc[k] += partials[((size_t)slot * maxch + c) * 3 + k];
+  __shared__ double sh[3][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 3; k++) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) sh[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[3];
+    for (int k = 0; k < 3; k++) {
+      tot[k] = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot[k] += sh[k][w];
+    }
+    epi_finalize<EPI>(sc[slot], tot);
+  }
+}
+
+inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_t st) {
+  TcChunks ch;
+  ch.nrhs = a.nrhs_tc;
+  for (int l = 0; l < MAXLAT; l++) ch.nch[l] = l < a.b.nlat ? a.b.lat[l].nchunk : 0;
+  const int nslot = a.b.nlat * a.nrhs_tc;
+  switch (epi) {
+    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    default: return cudaSuccess;
+  }
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, cudaStream_t st);
+
+#define WCL_MRHS_CASE(P, DAG, MODE, EPI)                                                         \
+  case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                                \
+    dslash_mrhs_kernel<P, DAG, MODE, EPI><<<a.b.total_blocks, threads, 0, st>>>(a);             \
+    fin = EPI;                                                                                  \
+    break;
+
+#define WCL_DEFINE_MRHS_LAUNCHER(P)                                                              \
+  template <>                                                                                    \
+  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, cudaStream_t st) { \
+    const int threads = MR_SITES * a.nrhs_tc;                                                    \
+    int fin = 0;                                                                                 \
+    switch (mode | (dagger ? 16 : 0)) {                                                          \
+      WCL_MRHS_CASE(P, false, MODE_POST, EPI_NONE)                                               \
+      WCL_MRHS_CASE(P, true, MODE_POST, EPI_NONE)                                                \
+      WCL_MRHS_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_NONE)                                    \
+      WCL_MRHS_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_NONE)                                     \
+      WCL_MRHS_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_ALPHA)                                   \
+      WCL_MRHS_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_OMEGA)                                   \
+      WCL_MRHS_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_CGALPHA)                                 \
+      WCL_MRHS_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_CGZ)                                      \
+      default: return cudaErrorInvalidValue;                                                     \
+    }                                                                                            \
+    cudaError_t e = cudaGetLastError();                                                          \
+    if (e != cudaSuccess) return e;                                                              \
+    return launch_epi_finalize(fin, a, st);                                                      \
+  }
+
 // host-side launchers (one instantiation set per precision translation unit)
 template <int P>
 cudaError_t launch_dslash(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st);
 template <int P>
 cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
+
+// the double-float operator only serves source preparation and residual replacement
+#define WCL_DEFINE_DSLASH_LAUNCHERS_DF(P)                                                           \
+  template <>                                                                                       \
+  cudaError_t launch_dslash<P>(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st) { \
+    dim3 grid(a.b.total_blocks), blk(block);                                                        \
+    switch (mode | (dagger ? 16 : 0)) {                                                             \
+      WCL_DSLASH_CASE(P, false, MODE_POST, EPI_NONE)                                                \
+      WCL_DSLASH_CASE(P, true, MODE_POST, EPI_NONE)                                                 \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_NONE)                                     \
+      WCL_DSLASH_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_NONE)                                      \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY, EPI_NONE)                                                \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON, EPI_NONE)            \
+      default: return cudaErrorInvalidValue;                                                        \
+    }                                                                                               \
+    return cudaGetLastError();                                                                      \
+  }                                                                                                 \
+  template <>                                                                                       \
+  cudaError_t launch_clover<P>(const CloverArgs& a, int block, cudaStream_t st) {                   \
+    clover_kernel<P><<<a.b.total_blocks, block, 0, st>>>(a);                                        \
+    return cudaGetLastError();                                                                      \
+  }
 
 #define WCL_DSLASH_CASE(P, DAG, MODE, EPI)                                            \
   case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                       \

@@ -3,4 +3,5 @@
 
 namespace wcl {
 WCL_DEFINE_DSLASH_LAUNCHERS(F32)
+WCL_DEFINE_MRHS_LAUNCHER(F32)
 }  // namespace wcl

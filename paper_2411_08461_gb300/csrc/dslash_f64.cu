@@ -3,4 +3,5 @@
 
 namespace wcl {
 WCL_DEFINE_DSLASH_LAUNCHERS(F64)
+WCL_DEFINE_MRHS_LAUNCHER(F64)
 }  // namespace wcl

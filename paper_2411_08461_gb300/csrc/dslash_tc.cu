@@ -505,39 +505,6 @@ __global__ void __launch_bounds__(TC_WARPS * 32) dslash_tc_kernel(const __grid_c
   }
 }
 
-// sum the per-CTA partials of every slot and run the finaliser (one block per slot)
-struct TcChunks {
-  int nch[MAXLAT];  // CTAs (partials) per lattice
-  int nrhs;
-};
-
-template <int EPI>
-__global__ void __launch_bounds__(256) tc_epi_finalize_kernel(const double* __restrict__ partials, int maxch,
-                                                              TcChunks ch, const int* __restrict__ active,
-                                                              Scalars* sc) {
-  const int slot = blockIdx.x;
-  if (active && !active[slot]) return;
-  const int n = ch.nch[slot / ch.nrhs];
-  double acc[3] = {0, 0, 0};
-  for (int c = threadIdx.x; c < n; c += blockDim.x)
-    for (int k = 0; k < 3; k++) acc[k] += partials[((size_t)slot * maxch + c) * 3 + k];
-  __shared__ double sh[3][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 3; k++) {
-    double v = warp_sum(acc[k]);
-    if (lane == 0) sh[k][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot[3];
-    for (int k = 0; k < 3; k++) {
-      tot[k] = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot[k] += sh[k][w];
-    }
-    epi_finalize<EPI>(sc[slot], tot);
-  }
-}
-
 #define WCL_TC_CASE(DAG, MODE, EPI)                                                        \
   case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                          \
     dslash_tc_kernel<P, DAG, MODE, EPI><<<a.b.total_blocks, TC_WARPS * 32, 0, st>>>(a);   \
@@ -559,18 +526,8 @@ cudaError_t launch_dslash_tc_p(const DslashArgs& a, bool dagger, int mode, cudaS
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || fin == EPI_NONE) return e;
-  TcChunks ch;
-  ch.nrhs = a.nrhs_tc;
-  for (int l = 0; l < MAXLAT; l++) ch.nch[l] = l < a.b.nlat ? a.b.lat[l].nchunk : 0;
-  const int nslot = a.b.nlat * a.nrhs_tc;
-  switch (fin) {
-    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-  }
-  return cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_epi_finalize(fin, a, st);
 }
 
 cudaError_t launch_dslash_tc(int prec, const DslashArgs& a, bool dagger, int mode, cudaStream_t st) {

@@ -33,7 +33,62 @@ namespace wcl {
 
 constexpr int MAXLAT = 8;
 
-enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, DF64 = 4 };
+// DF64: the FP64 fields read into double-float arithmetic (see dfloat below);
+// used for intermediate residual replacements, never for a reported result.
+
+// ---------------------------------------------------------------------------
+// double-float: value = hi + lo, |lo| <= ulp(hi)/2, a ~48-bit significand on the
+// FP32 pipes (Dekker 1971; Knuth's two-sum and the FMA two-product).  On GB300
+// FP32 issue is many times the FP64 rate, so this is the cheap way to apply the
+// operator with far more than FP32 accuracy.
+struct dfloat {
+  float hi, lo;
+  __host__ __device__ __forceinline__ dfloat() {}
+  __host__ __device__ __forceinline__ dfloat(float x) : hi(x), lo(0.f) {}
+  __host__ __device__ __forceinline__ dfloat(int x) : hi((float)x), lo(0.f) {}
+  __host__ __device__ __forceinline__ dfloat(double d) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+  }
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dfloat df_quick(float s, float e) {  // |s| >= |e|
+  dfloat r;
+  r.hi = __fadd_rn(s, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  float s, e;
+  df_two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_quick(s, e);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) {
+  dfloat r;
+  r.hi = -a.hi;
+  r.lo = -a.lo;
+  return r;
+}
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+// keep the floating-point fma visible next to the double-float one
+__host__ __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__host__ __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 
 template <typename R>
 struct cpx {
@@ -116,6 +171,15 @@ struct Traits<BF16> {
   static constexpr bool HAS_NORM = true;
 };
 
+template <>
+struct Traits<DF64> {
+  using R = dfloat;  // storage is the FP64 layout
+  static constexpr int SP_CHUNK = 12, SP_CHUNK_BYTES = 16;
+  static constexpr int LK_CHUNK = 9, LK_CHUNK_BYTES = 16;
+  static constexpr int CL_CHUNK = 36, CL_CHUNK_BYTES = 16;
+  static constexpr bool HAS_NORM = false;
+};
+
 inline int prec_spinor_bytes_per_site(int p) {
   switch (p) {
     case F64: return 192;
@@ -185,6 +249,25 @@ struct SpinorIO<F64> {
     double2* p = static_cast<double2*>(base);
 #pragma unroll
     for (int k = 0; k < 12; k++) p[k * stride + i] = make_double2(v[k].re, v[k].im);
+  }
+};
+
+template <>
+struct SpinorIO<DF64> {
+  using R = dfloat;
+  template <bool NC = true>
+  __device__ static void load(cpx<R> v[12], const void* base, const float*, long stride, long i) {
+    const double2* p = static_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      double2 d = ld<NC>(p + k * stride + i);
+      v[k] = {dfloat(d.x), dfloat(d.y)};
+    }
+  }
+  __device__ static void store(const cpx<R> v[12], void* base, float*, long stride, long i) {
+    double2* p = static_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) p[k * stride + i] = make_double2((double)v[k].re, (double)v[k].im);
   }
 };
 
@@ -274,6 +357,18 @@ struct LinkIO<F64> {
   }
 };
 template <>
+struct LinkIO<DF64> {
+  using R = dfloat;
+  __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
+    const double2* p = static_cast<const double2*>(base) + (long)mu * 9 * stride;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      double2 d = ldg(p + k * stride + i);
+      u[k / 3][k % 3] = {dfloat(d.x), dfloat(d.y)};
+    }
+  }
+};
+template <>
 struct LinkIO<F32> {
   using R = float;
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
@@ -349,6 +444,30 @@ struct CloverIO<F64> {
       for (int k = 0; k < 15; k++) {
         double2 v = ldg(p + (18 * b + 3 + k) * stride + i);
         L[k] = {v.x, v.y};
+      }
+      hermitian6_apply(y + 6 * b, d, L, x + 6 * b);
+    }
+  }
+};
+template <>
+struct CloverIO<DF64> {
+  using R = dfloat;
+  __device__ static void apply(cpx<R> y[12], const cpx<R> x[12], const void* base, const float*, long stride, long i) {
+    const double2* p = static_cast<const double2*>(base);
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+      R d[6];
+      cpx<R> L[15];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        double2 v = ldg(p + (18 * b + k) * stride + i);
+        d[2 * k] = dfloat(v.x);
+        d[2 * k + 1] = dfloat(v.y);
+      }
+#pragma unroll
+      for (int k = 0; k < 15; k++) {
+        double2 v = ldg(p + (18 * b + 3 + k) * stride + i);
+        L[k] = {dfloat(v.x), dfloat(v.y)};
       }
       hermitian6_apply(y + 6 * b, d, L, x + 6 * b);
     }

@@ -20,10 +20,11 @@ STATUS_NAMES = {
     5: "WCL_ERR_BREAKDOWN", 6: "WCL_ERR_NONFINITE", 7: "WCL_ERR_RECONSTRUCT", 8: "WCL_ERR_TIMEOUT",
     9: "WCL_ERR_NO_GAUGE", 10: "WCL_ERR_NO_PRECOND",
 }
-PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3}
 PTC_NWEIGHTS = 5760
 WCL_OPT_TENSOR_CORES = 1
+WCL_OPT_SHARED_LINKS = 2
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 

@@ -1,7 +1,7 @@
 """Shared helpers for the GPU parity tests (build once, move arrays, normwise errors)."""
 import numpy as np
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3, "bf16": 5e-3}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-5, "f16": 5e-3, "bf16": 5e-3}
 
 
 def built():

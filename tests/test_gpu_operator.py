@@ -30,7 +30,7 @@ def _setup(pkg, dims, eps=0.3, seed=0, kappa=0.1235, csw=1.0, tb=-1):
     return ctx, op, gauge
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("dims", SHAPES)
 def test_apply_D_parity(pkg, dims, prec):
     ctx, op, _ = _setup(pkg, dims, seed=1)
@@ -53,7 +53,7 @@ def test_apply_D_time_boundary_and_csw(pkg, tb):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_apply_Mpc_parity(pkg, prec, dagger):
     dims = (6, 4, 2, 8)
@@ -125,4 +125,42 @@ def test_tensor_core_and_per_thread_kernels_agree(pkg):
         ctx.wcl_apply_Mpc(o, psi, "f16", nrhs=12)
         outs.append(host(o))
     assert relerr(outs[0], outs[1]) <= 5e-3
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((2, 2, 2, 2), 16), ((8, 4, 4, 6), 7)])
+def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec):
+    """Multi-RHS Schur operator with links and clover staged in shared memory (16-site tiles,
+    ragged last tile for Vh = 96, 1296, 8, 384) against the oracle, RHS of very different size."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+
+    ctx, op, _ = _setup(pkg, dims, seed=17)
+    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, 1)
+    psi = W.gaussian_fermion(dims, 18, nrhs=nrhs)[:, 0].copy()
+    psi[1] *= 1e-7
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs, dagger=dagger)
+    got = host(out)
+    for k in range(nrhs):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL[prec], k
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_shared_links_and_per_thread_kernels_agree(pkg, prec):
+    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+
+    dims = (8, 8, 8, 16)
+    ctx, _, _ = _setup(pkg, dims, seed=19)
+    psi = cuda(W.gaussian_fermion(dims, 20, nrhs=12)[:, 0].copy())
+    outs = []
+    for sl in (1, 0):
+        ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, sl)
+        o = cuda(np.zeros(psi.shape, dtype=np.complex128))
+        ctx.wcl_apply_Mpc(o, psi, prec, nrhs=12)
+        outs.append(host(o))
+    # same arithmetic in the same order: identical up to FMA contraction differences
+    assert relerr(outs[0], outs[1]) <= (1e-14 if prec == "f64" else 1e-6)
     ctx.close()

@@ -97,6 +97,35 @@ def test_batch_of_uneven_lattices(pkg):
         c.close()
 
 
+@pytest.mark.parametrize("shared_links", [1, 0])
+@pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
+def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
+    """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials)."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+
+    shapes = [(4, 4, 4, 8), (6, 6, 2, 10)]
+    ctxs, ops, bs, xs = [], [], [], []
+    for k, dims in enumerate(shapes):
+        g = W.gauge_links(dims, 0.3, 30 + k)
+        c = pkg.Context(dims)
+        c.wcl_set_option(WCL_OPT_SHARED_LINKS, shared_links)
+        c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
+        ctxs.append(c)
+        ops.append(dirac.from_qdp_problem(g, dims, 0.1235, 1.0))
+        b = W.z2_fermion(dims, 40 + k, nrhs=4)
+        b[2] *= 1e3
+        bs.append(b)
+        xs.append(cuda(np.zeros_like(b)))
+    _, info = pkg.wcl_invert_batch(ctxs, xs, [cuda(b) for b in bs], 4,
+                                   pkg.wcl_default_params(solver=solver, sloppy="f32", tol=1e-10))
+    for k in range(len(shapes)):
+        xh = host(xs[k])
+        for r in range(4):
+            assert _oracle_true_residual(ops[k], xh[r], bs[k][r]) <= 1e-10, (k, r, info)
+    for c in ctxs:
+        c.close()
+
+
 def test_zero_source_gives_zero(pkg):
     dims = (4, 4, 4, 4)
     ctx = pkg.Context(dims)
