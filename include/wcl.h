@@ -213,9 +213,17 @@ typedef enum {
                               multiplies on the tensor cores (mma.sync, FP32 accumulation);
                               0 (default): the per-thread kernel, faster with this field layout */
   ,
-  WCL_OPT_SHARED_LINKS = 2 /* 1 (default): multi-RHS dslash (4..16 RHS, Schur operator) stages the
-                              links and clover of a 16-site tile in shared memory once for all RHS;
+  WCL_OPT_SHARED_LINKS = 2 /* 1 (default) or 16 or 32: the multi-RHS dslash (4..16 RHS, Schur
+                              operator) may stage the links and clover of a tile of sites in shared
+                              memory once for all RHS; the value is the tile (1 = 16 sites) used
+                              when the autotuner is off (FP64 always uses 16).
                               0: one thread per (site, RHS) reading its own links and clover */
+  ,
+  WCL_OPT_AUTOTUNE = 3 /* 1 (default): the first launch of each dslash configuration (precision,
+                          operator form, RHS count, lattice shapes) outside graph capture times
+                          every eligible kernel variant and launch shape and keeps the fastest
+                          for the process; the environment variable WCL_TUNE_CACHE=<file>
+                          makes the choices persist (text, appended).  0: fixed defaults */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */
@@ -229,6 +237,11 @@ typedef struct {
   long long dslash_timed;    /* how many dslash launches were timed */
   double dslash_bytes;       /* algorithmic bytes of the timed launches */
   double dslash_flops;       /* algorithmic flops of the timed launches (1320 + 504 per clover site) */
+  /* the timed launches split by arithmetic precision, indexed by wcl_prec (F64, F32, F16, BF16, DF64) */
+  double prec_ms[5];
+  long long prec_timed[5];
+  double prec_bytes[5];
+  double prec_flops[5];
 } wcl_stats;
 
 /* When enabled, every fused dslash launch on ctx is bracketed by CUDA events on

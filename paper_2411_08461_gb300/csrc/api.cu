@@ -46,7 +46,7 @@ bool valid_apply_prec(int p) { return p >= WCL_F64 && p <= WCL_DF64; }
 
 wcl_status alloc_lattice(wcl_ctx* c) {
   LatticeDevice& L = c->lat;
-  for (int pr = 0; pr < 4; pr++)
+  for (int pr = 0; pr < 5; pr++)
     for (int p = 0; p < 2; p++) {
       WCL_CUDA(cudaMalloc(&L.gauge[pr][p], gauge_parity_bytes(pr, L.stride)));
       WCL_CUDA(cudaMalloc(&L.clov[pr][p], clover_parity_bytes(pr, L.stride)));
@@ -61,7 +61,7 @@ wcl_status alloc_lattice(wcl_ctx* c) {
 
 void free_lattice(wcl_ctx* c) {
   LatticeDevice& L = c->lat;
-  for (int pr = 0; pr < 4; pr++)
+  for (int pr = 0; pr < 5; pr++)
     for (int p = 0; p < 2; p++) {
       cudaFree(L.gauge[pr][p]);
       cudaFree(L.clov[pr][p]);
@@ -242,7 +242,7 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
   WCL_CUDA(import_fermion(L, d_in, rs, L.vh * 12, nrhs, io.ptr[0], nullptr, c->stream));
   count_launch(c);
   count_launch(c);
-  if (prec == WCL_F64 || prec == WCL_DF64) {
+  if (prec == WCL_F64) {
     pe = ie, po = io, qe = oe, qo = oo;
   } else {
     WCL_CHECK(ws_field(v, "D_pin_e", prec, nrhs, &pe));
@@ -255,7 +255,7 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
   // out_p = A_pp in_p - kappa D_{p,1-p} in_{1-p}
   WCL_CHECK(dslash(v, prec, nrhs, qe, po, &pe, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
   WCL_CHECK(dslash(v, prec, nrhs, qo, pe, &po, 1, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
-  if (prec != WCL_F64 && prec != WCL_DF64) {
+  if (prec != WCL_F64) {
     WCL_CHECK(convert(v, F64, prec, nrhs, oe, qe, nullptr));
     WCL_CHECK(convert(v, F64, prec, nrhs, oo, qo, nullptr));
   }
@@ -281,7 +281,7 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
   std::vector<wcl_ctx*> v{c};
   const LatticeDevice& L = c->lat;
   FieldRef ie, oe, pe, qe, tmp;
-  const bool fp64_fields = prec == WCL_F64 || prec == WCL_DF64;
+  const bool fp64_fields = prec == WCL_F64;
   WCL_CHECK(ws_field(v, "M_in", F64, nrhs, &ie));
   WCL_CHECK(ws_field(v, "M_out", F64, nrhs, &oe));
   WCL_CHECK(ws_field(v, "M_tmp", fp64_fields ? F64 : prec, nrhs, &tmp));
@@ -395,9 +395,15 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
   if (!c) return WCL_ERR_INVALID_ARG;
   switch (option) {
     case WCL_OPT_TENSOR_CORES: c->tensor_cores = value != 0; return WCL_OK;
-    case WCL_OPT_SHARED_LINKS: c->shared_links = value != 0; return WCL_OK;
+    case WCL_OPT_SHARED_LINKS:
+      if (value == 0 || value == 1 || value == 16 || value == 32) {
+        c->shared_links = value == 1 ? 16 : value;
+        return WCL_OK;
+      }
+      break;
+    case WCL_OPT_AUTOTUNE: c->autotune = value != 0; return WCL_OK;
   }
-  set_error("wcl_set_option: unknown option %d", option);
+  set_error("wcl_set_option: unknown option %d or value %d", option, value);
   return WCL_ERR_INVALID_ARG;
 }
 
@@ -415,9 +421,19 @@ wcl_status wcl_get_stats(wcl_ctx* c, wcl_stats* out, int reset) {
   out->dslash_timed = c->dslash_timed;
   out->dslash_bytes = c->dslash_bytes;
   out->dslash_flops = c->dslash_flops;
+  for (int k = 0; k < 5; k++) {
+    out->prec_ms[k] = c->prec_ms[k];
+    out->prec_timed[k] = c->prec_timed[k];
+    out->prec_bytes[k] = c->prec_bytes[k];
+    out->prec_flops[k] = c->prec_flops[k];
+  }
   if (reset) {
     c->kernel_launches = c->dslash_launches = c->dslash_timed = 0;
     c->dslash_ms = c->dslash_bytes = c->dslash_flops = 0;
+    for (int k = 0; k < 5; k++) {
+      c->prec_ms[k] = c->prec_bytes[k] = c->prec_flops[k] = 0;
+      c->prec_timed[k] = 0;
+    }
   }
   return WCL_OK;
 }

@@ -178,6 +178,27 @@ struct AddInto64 {  // x64 += xs; xs = 0
   }
 };
 
+template <int PX>
+struct AddInto64Split {  // x64 += xs; xs = 0; xdf = double-float copy of x64
+  FieldRef x64, xs, xdf;
+  __device__ void operator()(const Slice& s, const LatGeom& g, long i) const {
+    cpx<double> x[12];
+    cpx<typename Traits<PX>::R> d[12];
+    WCL_LD(F64, false, x, x64);
+    WCL_LD(PX, false, d, xs);
+    cpx<dfloat> xd[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x[k] = x[k] + cpx<double>{double(d[k].re), double(d[k].im)};
+      d[k] = {0, 0};
+      xd[k] = {dfloat(x[k].re), dfloat(x[k].im)};
+    }
+    WCL_ST(F64, x, x64);
+    WCL_ST(PX, d, xs);
+    WCL_ST(DF64, xd, xdf);
+  }
+};
+
 template <int P>
 struct Norm2 {  // aux[k] (=|+=) ||a - b||^2  (b optional)
   FieldRef a, b;
@@ -349,16 +370,34 @@ struct BicgUpdate {  // x += alpha p + omega s; r = s - omega t; then rho' and |
 // b_hat - M_hat x_e; rS = r64.  ro holds the odd residual b_o - (A_oo x_o - kappa D_oe x_e).
 // aux[0] = ||r_e||^2, aux[3] = ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true residual).
 // BiCGStab also recomputes rho against rhat (REPLACE).
-template <int S>
+// One field of precision Q (F64 or DF64) read as FP64 values.
+template <int Q>
+__device__ __forceinline__ void load_as_f64(cpx<double> v[12], const void* base, long stride, long i);
+template <>
+__device__ __forceinline__ void load_as_f64<F64>(cpx<double> v[12], const void* base, long stride, long i) {
+  SpinorIO<F64>::load<false>(v, base, nullptr, stride, i);
+}
+template <>
+__device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void* base, long stride, long i) {
+  cpx<dfloat> d[12];
+  SpinorIO<DF64>::load<false>(d, base, nullptr, stride, i);
+#pragma unroll
+  for (int k = 0; k < 12; k++) v[k] = {double(d[k].re), double(d[k].im)};
+}
+
+// r64 holds the operator result A_ee x_e - kappa D_eo x_o in precision Q and is
+// overwritten, in place, by the FP64 residual b_hat - (that); ro holds the odd
+// residual of the reconstruction (precision Q).
+template <int S, int Q>
 struct ResidualReplace {
   FieldRef r64, bhat, rS, rhat, ro;
   int bicg;  // 1: BiCGStab rho REPLACE finalize; 0: CG (only the norm)
   __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
     using R = typename Traits<S>::R;
     cpx<double> y[12], b[12];
-    WCL_LD(F64, true, b, ro);
+    load_as_f64<Q>(b, rhs_ptr<Q>(ro, s.l, s.rhs, g.stride), g.stride, i);
     acc[3] += norm_site(b);
-    WCL_LD(F64, false, y, r64);
+    load_as_f64<Q>(y, rhs_ptr<Q>(r64, s.l, s.rhs, g.stride), g.stride, i);
     WCL_LD(F64, true, b, bhat);
     cpx<R> rs[12];
 #pragma unroll

@@ -118,27 +118,132 @@ bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode) {
 }
 
 bool use_mrhs(const wcl_ctx* c, int prec, int nrhs, int mode) {
-  return c->shared_links && prec != DF64 && nrhs >= 4 && nrhs * MR_SITES <= 256 &&
+  return c->shared_links && prec != DF64 && nrhs >= 4 && nrhs <= 16 &&
          (mode == MODE_POST || mode == (MODE_XPAY | MODE_PRE));
 }
 
 int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
-  // smallest site tile any dslash kernel may use, so that the partials fit every variant
-  const int block = std::min(ctxs[0]->dslash_block[prec], std::min(tc_tile_sites(), MR_SITES));
+  // smallest site tile any dslash variant may use, so that the partials fit every variant
+  (void)prec;
+  const int block = std::min(kTuneMinBlock, std::min(tc_tile_sites(), MR_SITES));
   long m = 1;
   for (auto* c : ctxs) m = std::max(m, (c->lat.vh + block - 1) / block);
   return (int)m;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel variants of one dslash configuration and their launch.
+static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, DslashArgs a, bool dagger,
+                                  int mode, TuneChoice ch, cudaStream_t st) {
+  if (ch.variant == V_THREAD) {
+    a.b = make_batch(ctxs, nrhs, ch.block, 0);
+    switch (prec) {
+      case F64: return launch_dslash<F64>(a, dagger, mode, ch.block, st);
+      case DF64: return launch_dslash<DF64>(a, dagger, mode, ch.block, st);
+      case F32: return launch_dslash<F32>(a, dagger, mode, ch.block, st);
+      case F16: return launch_dslash<F16>(a, dagger, mode, ch.block, st);
+      default: return launch_dslash<BF16>(a, dagger, mode, ch.block, st);
+    }
+  }
+  // one CTA covers all right-hand sides of its sites
+  const int ts = ch.variant == V_TC ? tc_tile_sites() : ch.block;
+  a.b = make_batch(ctxs, 1, ts, 0);
+  for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
+  a.nrhs_tc = nrhs;
+  if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
+  switch (prec) {
+    case F64: return launch_dslash_mrhs<F64>(a, dagger, mode, ts, st);
+    case F32: return launch_dslash_mrhs<F32>(a, dagger, mode, ts, st);
+    case F16: return launch_dslash_mrhs<F16>(a, dagger, mode, ts, st);
+    default: return launch_dslash_mrhs<BF16>(a, dagger, mode, ts, st);
+  }
+}
+
+static bool same_ptr(const FieldRef& w, const FieldRef& r, int nlat) {
+  for (int l = 0; l < nlat; l++)
+    if (w.ptr[l] && w.ptr[l] == r.ptr[l]) return true;
+  return false;
+}
+
+// Pick the variant for this configuration: from the cache, else by timing every
+// candidate (without the fused reduction, whose result must be produced once).
+static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const DslashArgs& a,
+                                 bool dagger, int mode) {
+  wcl_ctx* c0 = ctxs[0];
+  const int nlat = (int)ctxs.size();
+  const bool tc_ok = use_tc(c0, prec, nrhs, mode);
+  const bool mr_ok = use_mrhs(c0, prec, nrhs, mode);
+  TuneChoice dflt{V_THREAD, c0->dslash_block[prec == DF64 ? F64 : prec]};
+  if (tc_ok)
+    dflt = {V_TC, tc_tile_sites()};
+  else if (mr_ok)
+    dflt = {V_SMEM, prec == F64 ? 16 : c0->shared_links};
+  std::string key = "dslash p" + std::to_string(prec) + " m" + std::to_string(mode) + " d" + std::to_string(dagger) +
+                    " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok);
+  for (auto* c : ctxs)
+    key += " " + std::to_string(c->lat.dims[0]) + "x" + std::to_string(c->lat.dims[1]) + "x" +
+           std::to_string(c->lat.dims[2]) + "x" + std::to_string(c->lat.dims[3]);
+  TuneChoice ch;
+  if (tune_lookup(key, &ch)) return ch;
+  // only time when the launches may be repeated: outside graph capture, outputs not read
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c0->stream, &cs);
+  if (!c0->autotune || c0->capturing || cs != cudaStreamCaptureStatusNone || same_ptr(a.out, a.in, nlat) ||
+      same_ptr(a.out, a.x, nlat) || same_ptr(a.out, a.f, nlat) || same_ptr(a.out2, a.in, nlat) ||
+      same_ptr(a.out2, a.x, nlat) || same_ptr(a.out2, a.f, nlat))
+    return dflt;
+  std::vector<TuneChoice> cand;
+  for (int blk : {64, 128, 256, 512}) cand.push_back({V_THREAD, blk});
+  if (mr_ok) {
+    cand.push_back({V_SMEM, 16});
+    if (prec != F64) cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
+  }
+  if (tc_ok) cand.push_back({V_TC, tc_tile_sites()});
+  const int plain_mode = mode & 31;  // without the fused reduction
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return dflt;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return dflt;
+  }
+  float best = 1e30f;
+  TuneChoice pick = dflt;
+  for (const TuneChoice& c : cand) {
+    if (launch_variant(ctxs, prec, nrhs, a, dagger, plain_mode, c, c0->stream) != cudaSuccess) {
+      cudaGetLastError();  // launch-configuration errors are not sticky: skip the candidate
+      continue;
+    }
+    count_launch(c0, true);
+    cudaEventRecord(e0, c0->stream);
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; r++) {
+      ok = launch_variant(ctxs, prec, nrhs, a, dagger, plain_mode, c, c0->stream) == cudaSuccess;
+      count_launch(c0, true);
+    }
+    cudaEventRecord(e1, c0->stream);
+    float ms = 0;
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tune_store(key, pick, best / 3);
+  return pick;
 }
 
 wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, const FieldRef& out, const FieldRef& in,
                      const FieldRef* x, const FieldRef* out2, int out_parity, bool dagger, CloverSel post,
                      CloverSel pre, Coef alpha, Coef beta, const int* active, const EpiSpec* epi) {
   wcl_ctx* c0 = ctxs[0];
-  const int dp = prec == DF64 ? F64 : prec;  // data precision (double-float reads the FP64 fields)
-  const int block = c0->dslash_block[dp];
+  const int dp = prec;
   DslashArgs a;
   memset(&a, 0, sizeof a);
-  a.b = make_batch(ctxs, nrhs, block, 0);
   a.out = out;
   a.in = in;
   if (x) a.x = *x;
@@ -175,47 +280,13 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
   if (x) mode |= MODE_XPAY;
   if (x && pre) mode |= MODE_PRE;
   if (out2) mode |= MODE_RECON;
-  const bool tc = use_tc(c0, prec, nrhs, mode);
-  const bool mr = !tc && use_mrhs(c0, prec, nrhs, mode);
-  if (mr) {
-    a.b = make_batch(ctxs, 1, MR_SITES, 0);  // one CTA covers all right-hand sides of its sites
-    for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
-    a.nrhs_tc = nrhs;
-  }
-  if (tc) {
-    a.b = make_batch(ctxs, 1, tc_tile_sites(), 0);  // one CTA covers all right-hand sides of its sites
-    for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
-    a.nrhs_tc = nrhs;
-  }
+  const TuneChoice ch = choose_variant(ctxs, prec, nrhs, a, dagger, mode);
   if (epi) mode |= epi->kind << 5;
   wcl_ctx::Timed* t = prof_begin(c0);
-  cudaError_t e;
-  if (tc) {
-    e = launch_dslash_tc(prec, a, dagger, mode, c0->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core dslash launch");
-    count_launch(c0, true);
-    if (epi && epi->kind != EPI_NONE) count_launch(c0);
-  } else if (mr) {
-    switch (prec) {
-      case F64: e = launch_dslash_mrhs<F64>(a, dagger, mode, c0->stream); break;
-      case F32: e = launch_dslash_mrhs<F32>(a, dagger, mode, c0->stream); break;
-      case F16: e = launch_dslash_mrhs<F16>(a, dagger, mode, c0->stream); break;
-      default: e = launch_dslash_mrhs<BF16>(a, dagger, mode, c0->stream); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "multi-RHS dslash launch");
-    count_launch(c0, true);
-    if (epi && epi->kind != EPI_NONE) count_launch(c0);
-  } else switch (prec) {
-    case F64: e = launch_dslash<F64>(a, dagger, mode, block, c0->stream); break;
-    case DF64: e = launch_dslash<DF64>(a, dagger, mode, block, c0->stream); break;
-    case F32: e = launch_dslash<F32>(a, dagger, mode, block, c0->stream); break;
-    case F16: e = launch_dslash<F16>(a, dagger, mode, block, c0->stream); break;
-    default: e = launch_dslash<BF16>(a, dagger, mode, block, c0->stream); break;
-  }
-  if (!tc && !mr) {
-    if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
-    count_launch(c0, true);
-  }
+  const cudaError_t e = launch_variant(ctxs, prec, nrhs, a, dagger, mode, ch, c0->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dslash launch");
+  count_launch(c0, true);
+  if (ch.variant != V_THREAD && epi && epi->kind != EPI_NONE) count_launch(c0);  // finaliser
   if (t) {
     cudaEventRecord(t->b, c0->stream);
     double sp, lk, cl;
@@ -227,6 +298,7 @@ wcl_status dslash_ex(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, cons
     double per_rhs = per - per_site_shared;
     double base_sites = sites / nrhs;
     t->bytes = base_sites * per_site_shared + sites * per_rhs;
+    t->prec = prec;
     t->flops = sites * (1320.0 + (post ? 504.0 : 0.0) + ((x && pre) ? 504.0 : 0.0) + (x ? 48.0 : 0.0));
   }
   return WCL_OK;
@@ -242,7 +314,7 @@ wcl_status clover_apply(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, c
   a.out = out;
   a.x = x;
   a.active = active;
-  const int dp = prec == DF64 ? F64 : prec;
+  const int dp = prec;
   for (size_t l = 0; l < ctxs.size(); l++) {
     const LatticeDevice& L = ctxs[l]->lat;
     a.c[l] = which == CL_A ? L.clov[dp][parity] : L.clovinv[dp][parity];
@@ -287,7 +359,7 @@ wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrh
   const int block = c0->blas_block;
   Batch b = make_batch(ctxs, nrhs, block, RED_MAXCH);
   cudaError_t e = cudaErrorInvalidValue;
-  const int key = pout * 4 + pin;
+  const int key = (pout == DF64 || pin == DF64) ? 100 + pout * 8 + pin : pout * 4 + pin;
   switch (key) {
     case F32 * 4 + F64: e = run_convert<F32, F64>(b, out, in, active, block, c0->stream); break;
     case F16 * 4 + F64: e = run_convert<F16, F64>(b, out, in, active, block, c0->stream); break;
@@ -296,6 +368,8 @@ wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrh
     case F64 * 4 + F16: e = run_convert<F64, F16>(b, out, in, active, block, c0->stream); break;
     case F64 * 4 + BF16: e = run_convert<F64, BF16>(b, out, in, active, block, c0->stream); break;
     case F64 * 4 + F64: e = run_convert<F64, F64>(b, out, in, active, block, c0->stream); break;
+    case 100 + DF64 * 8 + F64: e = run_convert<DF64, F64>(b, out, in, active, block, c0->stream); break;
+    case 100 + F64 * 8 + DF64: e = run_convert<F64, DF64>(b, out, in, active, block, c0->stream); break;
     case F32 * 4 + F32: e = run_convert<F32, F32>(b, out, in, active, block, c0->stream); break;
     case F16 * 4 + F16: e = run_convert<F16, F16>(b, out, in, active, block, c0->stream); break;
     case BF16 * 4 + BF16: e = run_convert<BF16, BF16>(b, out, in, active, block, c0->stream); break;
@@ -314,6 +388,13 @@ static void accum(wcl_ctx* c, size_t from, size_t to) {
       c->dslash_timed++;
       c->dslash_bytes += c->ev_pool[k].bytes;
       c->dslash_flops += c->ev_pool[k].flops;
+      const int pr = c->ev_pool[k].prec;
+      if (pr >= 0 && pr < 5) {
+        c->prec_ms[pr] += ms;
+        c->prec_timed[pr]++;
+        c->prec_bytes[pr] += c->ev_pool[k].bytes;
+        c->prec_flops[pr] += c->ev_pool[k].flops;
+      }
     } else {
       cudaGetLastError();
     }

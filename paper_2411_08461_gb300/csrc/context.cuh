@@ -29,10 +29,13 @@ struct wcl_ctx {
   // counters and profiling
   long long kernel_launches = 0, dslash_launches = 0, dslash_timed = 0;
   double dslash_ms = 0, dslash_bytes = 0, dslash_flops = 0;
+  double prec_ms[5] = {}, prec_bytes[5] = {}, prec_flops[5] = {};
+  long long prec_timed[5] = {};
   bool profiling = false;
   struct Timed {
     cudaEvent_t a, b;
     double bytes, flops;
+    int prec;
   };
   std::vector<Timed> ev_pool;
   size_t ev_used = 0;
@@ -53,7 +56,9 @@ struct wcl_ctx {
   // launch shapes (picked by the tuner on first use)
   int dslash_block[4] = {128, 128, 128, 128};
   bool tensor_cores = false;  // multi-RHS 16-bit dslash on mma.sync (WCL_OPT_TENSOR_CORES)
-  bool shared_links = true;   // multi-RHS dslash with links/clover staged in shared memory
+  int shared_links = 16;      // multi-RHS dslash with links/clover staged in shared memory:
+                              // 0 off, else its sites per CTA when the tuner does not choose
+  bool autotune = true;       // time the dslash variants of a new configuration on first use
   int blas_block = 256;
 };
 
@@ -143,6 +148,19 @@ wcl_status convert(const std::vector<wcl_ctx*>& ctxs, int pout, int pin, int nrh
 cudaError_t launch_dslash_tc(int prec, const DslashArgs& a, bool dagger, int mode, cudaStream_t st);
 int tc_tile_sites();
 bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
+
+// Autotuner: the dslash variant of a configuration (precision, mode, RHS count,
+// lattice shapes, options) is picked by timing the candidates on first use and
+// kept for the process; with WCL_TUNE_CACHE=<file> choices persist across runs.
+enum TuneVariant { V_THREAD = 0, V_SMEM = 1, V_TC = 2 };
+struct TuneChoice {
+  int variant;  // TuneVariant
+  int block;    // threads per CTA (V_THREAD) or sites per CTA (V_SMEM, V_TC)
+};
+constexpr int kTuneMinBlock = 64;  // smallest per-thread block among the candidates
+bool tune_lookup(const std::string& key, TuneChoice* out);
+void tune_store(const std::string& key, TuneChoice c, float ms);
+void tune_clear();  // forget every choice of this process (the file is left as it is)
 bool use_mrhs(const wcl_ctx* c, int prec, int nrhs, int mode);
 
 // per-precision instantiations (defined in dslash_<prec>.cu)

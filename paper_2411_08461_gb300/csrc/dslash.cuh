@@ -289,13 +289,13 @@ __global__ void __launch_bounds__(256) clover_kernel(const __grid_constant__ Clo
 }
 
 // ---------------------------------------------------------------------------
-// Multi-RHS kernel: a CTA covers MR_SITES consecutive output sites and every
+// Multi-RHS kernel: a CTA covers TS (16 or 32) consecutive output sites and every
 // right-hand side.  Links and clover of the tile are read from memory once,
 // unpacked (12-real reconstruction, 16-bit scaling) into shared memory, and
-// reused by all RHS; each thread then computes one (site, rhs) pair.  Threads
-// of one RHS form a half warp.  Fused reductions write one partial per (RHS,
+// reused by all RHS, as are the neighbour indices; each thread then computes one
+// (site, rhs) pair.  The TS threads of one RHS are consecutive lanes of a warp.  Fused reductions write one partial per (RHS,
 // CTA) and are finalised by tc_epi_finalize_kernel.
-constexpr int MR_SITES = 16;
+constexpr int MR_SITES = 16;  // smallest tile (sizes the reduction partials)
 
 // Unpack chunk k of the packed clover term of site i into reals r[0..n) (n per chunk:
 // 2 for FP64, 4 for FP32, 8 for the 16-bit formats, which carry one scale per site).
@@ -341,8 +341,8 @@ struct CloverChunk<F16> : CloverChunk16<F16> {};
 template <>
 struct CloverChunk<BF16> : CloverChunk16<BF16> {};
 
-template <typename R>
-__device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[12], const R (*C)[MR_SITES], int ls) {
+template <typename R, int TS>
+__device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[12], const R (*C)[TS], int ls) {
 #pragma unroll
   for (int b = 0; b < 2; b++) {
     R d[6];
@@ -355,9 +355,9 @@ __device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[1
   }
 }
 
-template <int P, int MU, bool DAG>
+template <int P, int MU, bool DAG, int TS>
 __device__ __forceinline__ void hop_dir_smem(cpx<typename Traits<P>::R> acc[12], const void* in, const float* in_norm,
-                                             long stride, long jf, long jb, const typename Traits<P>::R (*U)[18][MR_SITES],
+                                             long stride, long jf, long jb, const typename Traits<P>::R (*U)[18][TS],
                                              int ls, typename Traits<P>::R sf, typename Traits<P>::R sb) {
   using R = typename Traits<P>::R;
   constexpr int SF = DAG ? +1 : -1;
@@ -405,32 +405,60 @@ __device__ __forceinline__ SiteNbr site_neighbours(const LatGeom& g, int p, long
   return n;
 }
 
-template <int P, bool DAG, int MODE, int EPI>
-__global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
+// Register cap: 16-site tiles (up to 256 threads) keep three CTAs per SM; 32-site
+// tiles (up to 512 threads) keep one CTA's registers within half the file for 12 RHS.
+template <int TS>
+struct MrhsBounds;
+template <>
+struct MrhsBounds<16> {
+  static constexpr int THREADS = 256, MIN_BLOCKS = 3;
+};
+template <>
+struct MrhsBounds<32> {
+  static constexpr int THREADS = 512, MIN_BLOCKS = 1;
+};
+
+template <int P, bool DAG, int MODE, int EPI, int TS>
+__global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsBounds<TS>::MIN_BLOCKS))
+    dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
   using R = typename Traits<P>::R;
   constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
-  __shared__ R Us[8][18][MR_SITES];
-  __shared__ R Cs[CLOV ? 72 : 1][MR_SITES];
+  __shared__ R Us[8][18][TS];             // links: 2 mu (fwd at the site), 2 mu + 1 (bwd at the neighbour)
+  __shared__ R Cs[CLOV ? 72 : 1][TS];     // unpacked clover, 72 reals per site
+  __shared__ int Nb[8][TS];               // neighbour indices within the other parity: 2 mu fwd, 2 mu + 1 bwd
+  __shared__ unsigned char Tb[TS];        // bit 0: forward t hop wraps, bit 1: backward t hop wraps
   const Slice s = find_slice(a.b, blockIdx.x);  // one slice per lattice
   const LatGeom& g = a.b.lat[s.l];
   const int nrhs = a.nrhs_tc;
   const int slot0 = s.l * nrhs;
   const int p = a.out_parity;
   const long stride = g.stride;
-  const long site0 = (long)s.chunk * MR_SITES;
+  const long site0 = (long)s.chunk * TS;
 
-  // phase 1: links (fwd at the site, bwd at the neighbour) and clover of the tile
-  for (int e = threadIdx.x; e < 8 * MR_SITES; e += blockDim.x) {
-    const int ls = e % MR_SITES, d = e / MR_SITES, mu = d >> 1;
+  // phase 0: coordinates and neighbours of the tile's sites, once for all RHS
+  if (threadIdx.x < TS) {
+    const long i = site0 + threadIdx.x;
+    if (i < g.vh) {
+      const SiteNbr n = site_neighbours(g, p, i);
+#pragma unroll
+      for (int mu = 0; mu < 4; mu++) {
+        Nb[2 * mu][threadIdx.x] = (int)n.jf[mu];
+        Nb[2 * mu + 1][threadIdx.x] = (int)n.jb[mu];
+      }
+      Tb[threadIdx.x] = (n.t + 1 == g.dims[3] ? 1 : 0) | (n.t == 0 ? 2 : 0);
+    }
+  }
+  __syncthreads();
+  // phase 1: links and clover of the tile, unpacked to R
+  for (int e = threadIdx.x; e < 8 * TS; e += blockDim.x) {
+    const int ls = e % TS, d = e / TS, mu = d >> 1;
     const long i = site0 + ls;
     cpx<R> u[3][3];
     if (i < g.vh) {
-      if (d & 1) {
-        const SiteNbr n = site_neighbours(g, p, i);
-        LinkIO<P>::load(u, a.gauge[s.l][1 - p], stride, n.jb[mu], mu);
-      } else {
+      if (d & 1)
+        LinkIO<P>::load(u, a.gauge[s.l][1 - p], stride, Nb[d][ls], mu);
+      else
         LinkIO<P>::load(u, a.gauge[s.l][p], stride, i, mu);
-      }
     } else {
 #pragma unroll
       for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {R(0), R(0)};
@@ -445,8 +473,8 @@ __global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant_
     using CC = CloverChunk<P>;
     const void* cb = (MODE & MODE_POST) ? a.cpost[s.l] : a.cpre[s.l];
     const float* cn = (MODE & MODE_POST) ? a.cpost_norm[s.l] : a.cpre_norm[s.l];
-    for (int e = threadIdx.x; e < CC::NCH * MR_SITES; e += blockDim.x) {
-      const int ls = e % MR_SITES, k = e / MR_SITES;
+    for (int e = threadIdx.x; e < CC::NCH * TS; e += blockDim.x) {
+      const int ls = e % TS, k = e / TS;
       const long i = site0 + ls;
       R r[CC::PER];
       if (i < g.vh) {
@@ -461,24 +489,24 @@ __global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant_
   }
   __syncthreads();
 
-  // phase 2: thread = (site ls, rhs)
-  const int ls = threadIdx.x & (MR_SITES - 1), rhs = threadIdx.x / MR_SITES;
+  // phase 2: thread = (site ls, rhs); the TS threads of one rhs are consecutive lanes
+  const int ls = threadIdx.x % TS, rhs = threadIdx.x / TS;
   const long i = site0 + ls;
   double red[3] = {0.0, 0.0, 0.0};
   const bool valid = rhs < nrhs && i < g.vh && (!a.active || a.active[slot0 + rhs]);
   if (valid) {
-    const SiteNbr n = site_neighbours(g, p, i);
     const void* in = rhs_ptr<P>(a.in, s.l, rhs, stride);
     const float* in_norm = rhs_norm(a.in, s.l, rhs, stride);
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
-    hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, n.jf[0], n.jb[0], Us, ls, R(1), R(1));
-    hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, n.jf[1], n.jb[1], Us, ls, R(1), R(1));
-    hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, n.jf[2], n.jb[2], Us, ls, R(1), R(1));
-    const R sf = (n.t + 1 == g.dims[3]) ? R(g.tb) : R(1);
-    const R sb = (n.t == 0) ? R(g.tb) : R(1);
-    hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, n.jf[3], n.jb[3], Us, ls, sf, sb);
+    hop_dir_smem<P, 0, DAG, TS>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us, ls, R(1), R(1));
+    hop_dir_smem<P, 1, DAG, TS>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us, ls, R(1), R(1));
+    hop_dir_smem<P, 2, DAG, TS>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us, ls, R(1), R(1));
+    const int tb = Tb[ls];
+    const R sf = (tb & 1) ? R(g.tb) : R(1);
+    const R sb = (tb & 2) ? R(g.tb) : R(1);
+    hop_dir_smem<P, 3, DAG, TS>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us, ls, sf, sb);
     const R alpha = R(a.alpha[s.l]);
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
@@ -488,7 +516,7 @@ __global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant_
       const R beta = R(a.beta[s.l]);
       if (MODE & MODE_PRE) {
         cpx<R> cx[12];
-        clover_apply_smem(cx, xv, Cs, ls);
+        clover_apply_smem<R, TS>(cx, xv, Cs, ls);
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * cx[k];
       } else {
@@ -508,18 +536,18 @@ __global__ void __launch_bounds__(256) dslash_mrhs_kernel(const __grid_constant_
     }
     if (MODE & MODE_POST) {
       cpx<R> y2[12];
-      clover_apply_smem(y2, acc, Cs, ls);
+      clover_apply_smem<R, TS>(y2, acc, Cs, ls);
       SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
     } else {
       SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
     }
   }
   if constexpr (EPI != EPI_NONE) {
-    // the MR_SITES threads of one rhs are one half warp
+    // the block size is a multiple of 32, so every lane of the warp takes part
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-      for (int o = MR_SITES / 2; o; o >>= 1) red[k] += __shfl_xor_sync(0xffffffffu, red[k], o);
+      for (int o = TS / 2; o; o >>= 1) red[k] += __shfl_xor_sync(0xffffffffu, red[k], o);
     if (ls == 0 && rhs < nrhs) {
       double* dst = a.partials + ((size_t)(slot0 + rhs) * a.maxch + s.chunk) * 3;
       dst[0] = red[0];
@@ -578,18 +606,22 @@ inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_
 }
 
 template <int P>
-cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, cudaStream_t st);
+cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st);
 
 #define WCL_MRHS_CASE(P, DAG, MODE, EPI)                                                         \
   case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                                \
-    dslash_mrhs_kernel<P, DAG, MODE, EPI><<<a.b.total_blocks, threads, 0, st>>>(a);             \
+    if (ts == 32)                                                                               \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 32><<<a.b.total_blocks, threads, 0, st>>>(a);       \
+    else                                                                                        \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 16><<<a.b.total_blocks, threads, 0, st>>>(a);       \
     fin = EPI;                                                                                  \
     break;
 
+// ts: sites per CTA (16 or 32); the geometry a.b must have been built with that tile
 #define WCL_DEFINE_MRHS_LAUNCHER(P)                                                              \
   template <>                                                                                    \
-  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, cudaStream_t st) { \
-    const int threads = MR_SITES * a.nrhs_tc;                                                    \
+  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st) { \
+    const int threads = (ts * a.nrhs_tc + 31) / 32 * 32;                                         \
     int fin = 0;                                                                                 \
     switch (mode | (dagger ? 16 : 0)) {                                                          \
       WCL_MRHS_CASE(P, false, MODE_POST, EPI_NONE)                                               \

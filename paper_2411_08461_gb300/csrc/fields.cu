@@ -346,6 +346,21 @@ static QdpGeom qgeom(const LatticeDevice& L) {
   return q;
 }
 
+// double-float copy: every FP64 real d becomes (hi, lo) = (fl(d), fl(d - fl(d)))
+__global__ void split_df64_kernel(const double2* __restrict__ src, float4* __restrict__ dst, long n) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const double2 d = src[k];
+    const float rh = (float)d.x, ih = (float)d.y;
+    dst[k] = make_float4(rh, (float)(d.x - (double)rh), ih, (float)(d.y - (double)ih));
+  }
+}
+
+static cudaError_t split_df64(const void* src, void* dst, size_t bytes, cudaStream_t st) {
+  const long n = (long)(bytes / 16);
+  split_df64_kernel<<<grid_for(n, 256), 256, 0, st>>>(static_cast<const double2*>(src), static_cast<float4*>(dst), n);
+  return cudaGetLastError();
+}
+
 cudaError_t import_gauge(const LatticeDevice& L, const void* d_qdp, int* d_flags, cudaStream_t st) {
   GaugePack gp;
   for (int p = 0; p < 2; p++) {
@@ -357,7 +372,10 @@ cudaError_t import_gauge(const LatticeDevice& L, const void* d_qdp, int* d_flags
   gp.stride = L.stride;
   gauge_import_kernel<<<grid_for(8 * L.vh, 256), 256, 0, st>>>(static_cast<const double2*>(d_qdp), qgeom(L), gp, 1e-12,
                                                                d_flags);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  for (int p = 0; p < 2 && e == cudaSuccess; p++)
+    e = split_df64(L.gauge[F64][p], L.gauge[DF64][p], gauge_parity_bytes(F64, L.stride), st);
+  return e;
 }
 
 cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw, int* d_flags,
@@ -377,6 +395,8 @@ cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa
           static_cast<uint4*>(inv ? L.clovinv[F16][p] : L.clov[F16][p]), nrm[F16 * 2 + p],
           static_cast<uint4*>(inv ? L.clovinv[BF16][p] : L.clov[BF16][p]), nrm[BF16 * 2 + p]);
       e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      e = split_df64(src, inv ? L.clovinv[DF64][p] : L.clov[DF64][p], clover_parity_bytes(F64, L.stride), st);
       if (e != cudaSuccess) return e;
     }
   }

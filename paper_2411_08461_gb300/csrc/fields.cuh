@@ -11,9 +11,10 @@ struct LatticeDevice {
   long stride = 0;      // padded sites per chunk
   double kappa = 0, csw = 0;
   bool loaded = false;
-  void* gauge[4][2] = {};    // [prec][parity]: 12-real links, [mu][chunk][stride]
-  void* clov[4][2] = {};     // [prec][parity]: A (packed Hermitian blocks)
-  void* clovinv[4][2] = {};  // [prec][parity]: A^-1
+  // [prec][parity], prec = F64, F32, F16, BF16, DF64 (the FP64 values split into float pairs)
+  void* gauge[5][2] = {};    // links, [mu][chunk][stride]; 18 reals (FP64, DF64) or 12 (row 2 rebuilt)
+  void* clov[5][2] = {};     // A (packed Hermitian blocks)
+  void* clovinv[5][2] = {};  // A^-1
   float* clov_norm[8] = {};  // [prec*2 + parity], half precisions only
   float* clovinv_norm[8] = {};
 };
@@ -21,21 +22,24 @@ struct LatticeDevice {
 // bytes of one parity-field chunk array for precision P (without norms)
 inline size_t spinor_field_bytes(int prec, long stride) {
   switch (prec) {
-    case F64: return (size_t)12 * 16 * stride;
+    case F64:
+    case DF64: return (size_t)12 * 16 * stride;
     case F32: return (size_t)6 * 16 * stride;
     default: return (size_t)3 * 16 * stride;
   }
 }
 inline size_t gauge_parity_bytes(int prec, long stride) {
   switch (prec) {
-    case F64: return (size_t)4 * 9 * 16 * stride;
+    case F64:
+    case DF64: return (size_t)4 * 9 * 16 * stride;
     case F32: return (size_t)4 * 3 * 16 * stride;
     default: return (size_t)4 * 3 * 8 * stride;
   }
 }
 inline size_t clover_parity_bytes(int prec, long stride) {
   switch (prec) {
-    case F64: return (size_t)36 * 16 * stride;
+    case F64:
+    case DF64: return (size_t)36 * 16 * stride;
     case F32: return (size_t)18 * 16 * stride;
     default: return (size_t)9 * 16 * stride;
   }

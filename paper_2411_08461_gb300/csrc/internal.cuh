@@ -53,6 +53,13 @@ struct dfloat {
   }
   __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
 };
+// a stored (hi, lo) pair, already normalised
+__host__ __device__ __forceinline__ dfloat df_pair(float hi, float lo) {
+  dfloat r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
 
 __device__ __forceinline__ dfloat df_quick(float s, float e) {  // |s| >= |e|
   dfloat r;
@@ -173,7 +180,7 @@ struct Traits<BF16> {
 
 template <>
 struct Traits<DF64> {
-  using R = dfloat;  // storage is the FP64 layout
+  using R = dfloat;  // storage: one float4 (re.hi, re.lo, im.hi, im.lo) per complex
   static constexpr int SP_CHUNK = 12, SP_CHUNK_BYTES = 16;
   static constexpr int LK_CHUNK = 9, LK_CHUNK_BYTES = 16;
   static constexpr int CL_CHUNK = 36, CL_CHUNK_BYTES = 16;
@@ -182,7 +189,8 @@ struct Traits<DF64> {
 
 inline int prec_spinor_bytes_per_site(int p) {
   switch (p) {
-    case F64: return 192;
+    case F64:
+    case DF64: return 192;
     case F32: return 96;
     default: return 48 + 4;
   }
@@ -257,17 +265,17 @@ struct SpinorIO<DF64> {
   using R = dfloat;
   template <bool NC = true>
   __device__ static void load(cpx<R> v[12], const void* base, const float*, long stride, long i) {
-    const double2* p = static_cast<const double2*>(base);
+    const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      double2 d = ld<NC>(p + k * stride + i);
-      v[k] = {dfloat(d.x), dfloat(d.y)};
+      const float4 f = ld<NC>(p + k * stride + i);
+      v[k] = {df_pair(f.x, f.y), df_pair(f.z, f.w)};
     }
   }
   __device__ static void store(const cpx<R> v[12], void* base, float*, long stride, long i) {
-    double2* p = static_cast<double2*>(base);
+    float4* p = static_cast<float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 12; k++) p[k * stride + i] = make_double2((double)v[k].re, (double)v[k].im);
+    for (int k = 0; k < 12; k++) p[k * stride + i] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
   }
 };
 
@@ -360,11 +368,11 @@ template <>
 struct LinkIO<DF64> {
   using R = dfloat;
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
-    const double2* p = static_cast<const double2*>(base) + (long)mu * 9 * stride;
+    const float4* p = static_cast<const float4*>(base) + (long)mu * 9 * stride;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      double2 d = ldg(p + k * stride + i);
-      u[k / 3][k % 3] = {dfloat(d.x), dfloat(d.y)};
+      const float4 f = ldg(p + k * stride + i);
+      u[k / 3][k % 3] = {df_pair(f.x, f.y), df_pair(f.z, f.w)};
     }
   }
 };
@@ -453,21 +461,21 @@ template <>
 struct CloverIO<DF64> {
   using R = dfloat;
   __device__ static void apply(cpx<R> y[12], const cpx<R> x[12], const void* base, const float*, long stride, long i) {
-    const double2* p = static_cast<const double2*>(base);
+    const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int b = 0; b < 2; b++) {
       R d[6];
       cpx<R> L[15];
 #pragma unroll
       for (int k = 0; k < 3; k++) {
-        double2 v = ldg(p + (18 * b + k) * stride + i);
-        d[2 * k] = dfloat(v.x);
-        d[2 * k + 1] = dfloat(v.y);
+        const float4 f = ldg(p + (18 * b + k) * stride + i);
+        d[2 * k] = df_pair(f.x, f.y);
+        d[2 * k + 1] = df_pair(f.z, f.w);
       }
 #pragma unroll
       for (int k = 0; k < 15; k++) {
-        double2 v = ldg(p + (18 * b + 3 + k) * stride + i);
-        L[k] = {dfloat(v.x), dfloat(v.y)};
+        const float4 f = ldg(p + (18 * b + 3 + k) * stride + i);
+        L[k] = {df_pair(f.x, f.y), df_pair(f.z, f.w)};
       }
       hermitian6_apply(y + 6 * b, d, L, x + 6 * b);
     }

@@ -35,11 +35,12 @@ struct KrylovSolver {
   wcl_solve_params prm;
   bool cg = false;
   bool gcr = false;
-  bool use_df = true;  // double-float operator for intermediate residual replacements
+  bool use_df = false;  // double-float operator for intermediate residual replacements
 
   FieldRef b_e, b_o, bhat, x, x_o, r64, tmp64;  // FP64
   FieldRef r, rhat, p, v, t, tmp;               // sloppy
   FieldRef xs;                                  // accumulator
+  FieldRef x_df, bo_df;                         // double-float copies of x and b_o
   Scalars* d_sc = nullptr;
   Scalars* h_sc = nullptr;
   int* d_active = nullptr;
@@ -80,6 +81,10 @@ struct KrylovSolver {
     WCL_CHECK(ws_field(ctxs, "t", S, nrhs, &t));
     WCL_CHECK(ws_field(ctxs, "tmp", S, nrhs, &tmp));
     WCL_CHECK(ws_field(ctxs, "xs", X, nrhs, &xs));
+    if (use_df) {
+      WCL_CHECK(ws_field(ctxs, "x_df", DF64, nrhs, &x_df));
+      WCL_CHECK(ws_field(ctxs, "bo_df", DF64, nrhs, &bo_df));
+    }
     void* q;
     WCL_CHECK(ws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
     d_sc = static_cast<Scalars*>(q);
@@ -216,10 +221,21 @@ struct KrylovSolver {
   // sloppy residual.  Two operator launches per update, in `oprec`: IEEE FP64,
   // or double-float (~48-bit) for a replacement in the middle of a solve.
   wcl_status reliable_update(bool restart, int oprec, const int* mask) {
+    const int bicg = (!cg && !restart) ? 1 : 0;
+    if (oprec == DF64) {
+      // double-float operator on double-float copies; x_o, tmp64 and r64 hold
+      // double-float values until ResidualReplace turns r64 into the FP64 residual
+      WCL_CHECK(map(AddInto64Split<X>{x, xs, x_df}, mask));
+      WCL_CHECK(dslash_ex(ctxs, DF64, nrhs, x_o, x_df, &bo_df, &tmp64, 1, false, CL_AINV, CL_A, C_KAPPA, C_ONE, mask));
+      WCL_CHECK(dslash(ctxs, DF64, nrhs, r64, x_o, &x_df, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, mask));
+      WCL_CHECK(reduce<4>(ResidualReplace<S, DF64>{r64, b_e, r, rhat, tmp64, bicg}, mask));
+      if (restart) WCL_CHECK(restart_krylov(mask));
+      return WCL_OK;
+    }
     WCL_CHECK(map(AddInto64<X>{x, xs}, mask));
-    WCL_CHECK(dslash_ex(ctxs, oprec, nrhs, x_o, x, &b_o, &tmp64, 1, false, CL_AINV, CL_A, C_KAPPA, C_ONE, mask));
-    WCL_CHECK(dslash(ctxs, oprec, nrhs, r64, x_o, &x, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, mask));
-    WCL_CHECK(reduce<4>(ResidualReplace<S>{r64, b_e, r, rhat, tmp64, (!cg && !restart) ? 1 : 0}, mask));
+    WCL_CHECK(dslash_ex(ctxs, F64, nrhs, x_o, x, &b_o, &tmp64, 1, false, CL_AINV, CL_A, C_KAPPA, C_ONE, mask));
+    WCL_CHECK(dslash(ctxs, F64, nrhs, r64, x_o, &x, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, mask));
+    WCL_CHECK(reduce<4>(ResidualReplace<S, F64>{r64, b_e, r, rhat, tmp64, bicg}, mask));
     if (restart) WCL_CHECK(restart_krylov(mask));
     return WCL_OK;
   }
@@ -438,6 +454,9 @@ struct KrylovSolver {
     cg = prm.solver == WCL_CGNR || gcr;  // GCR residual replacement keeps no BiCGStab state
     blk = c0->blas_block;
     bb = make_batch(ctxs, nrhs, blk, RED_MAXCH);
+    // Intermediate residual replacements of a mixed-precision solve use the
+    // double-float operator (FP32 pipes); every final one is IEEE FP64.
+    use_df = S != F64;
     WCL_CHECK(alloc());
     stop2.assign(nslot, 0);
     r2max.assign(nslot, 0);
@@ -447,9 +466,6 @@ struct KrylovSolver {
     status.assign(nslot, WCL_OK);
     WCL_CUDA(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * nslot, c0->stream));
     for (int s = 0; s < nslot; s++) h_active[s] = 1, h_upd[s] = h_updf[s] = h_upd64[s] = 0;
-    // Residual replacements stay in IEEE FP64: on GB300 the double-float operator
-    // measured twice as slow as FP64 (15.3 vs 7.9 ms for 12 RHS on 24^3x48).
-    use_df = false;
     WCL_CHECK(push_masks());
     WCL_CUDA(cudaMemsetAsync(c0->d_flags, 0, sizeof(int), c0->stream));
 
@@ -465,9 +481,17 @@ struct KrylovSolver {
     // b_hat = b_e + kappa D_eo A_oo^-1 b_o
     // (double-float operator: b_hat only seeds the iteration; every reported
     // residual is evaluated from b itself in FP64)
-    const int sprec = use_df ? DF64 : F64;
-    WCL_CHECK(clover_apply(ctxs, sprec, nrhs, tmp64, b_o, 1, CL_AINV, nullptr));
-    WCL_CHECK(dslash(ctxs, sprec, nrhs, bhat, tmp64, &b_e, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
+    if (use_df) {
+      // b_e's double-float copy goes to r64 and b_hat's to x_o (both free until the first update)
+      WCL_CHECK(convert(ctxs, DF64, F64, nrhs, bo_df, b_o, nullptr));
+      WCL_CHECK(convert(ctxs, DF64, F64, nrhs, r64, b_e, nullptr));
+      WCL_CHECK(clover_apply(ctxs, DF64, nrhs, tmp64, bo_df, 1, CL_AINV, nullptr));
+      WCL_CHECK(dslash(ctxs, DF64, nrhs, x_o, tmp64, &r64, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
+      WCL_CHECK(convert(ctxs, F64, DF64, nrhs, bhat, x_o, nullptr));
+    } else {
+      WCL_CHECK(clover_apply(ctxs, F64, nrhs, tmp64, b_o, 1, CL_AINV, nullptr));
+      WCL_CHECK(dslash(ctxs, F64, nrhs, bhat, tmp64, &b_e, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
+    }
     WCL_CHECK(reduce<1>(Norm2<F64>{b_e, b_e, 2, 0, 0}, nullptr));
     WCL_CHECK(reduce<1>(Norm2<F64>{b_o, b_o, 2, 1, 0}, nullptr));
     WCL_CHECK(reduce<1>(Norm2<F64>{bhat, bhat, 1, 0, 0}, nullptr));
@@ -506,6 +530,12 @@ struct KrylovSolver {
     if (gcr) WCL_CHECK(loop_gcr(nactive, prm.solver == WCL_FGCR_LEARNED));
     // events inside captured graphs cannot be timed: profiling launches directly
     bool graphs = prm.use_graphs != 0 && !c0->profiling;
+    if (graphs && !gcr) {
+      // let the tuner see the operator launches of the loop before they are captured
+      // (p is zero and v, t, tmp are overwritten by the first iteration)
+      WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, false, d_active));
+      if (cg) WCL_CHECK(apply_mhat(ctxs, S, nrhs, v, p, tmp, true, d_active));
+    }
     while (nactive > 0) {
       if (graphs && !gexec) {
         wcl_status s = capture(ce);

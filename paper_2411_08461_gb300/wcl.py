@@ -25,6 +25,7 @@ SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3}
 PTC_NWEIGHTS = 5760
 WCL_OPT_TENSOR_CORES = 1
 WCL_OPT_SHARED_LINKS = 2
+WCL_OPT_AUTOTUNE = 3
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 
@@ -47,6 +48,8 @@ class wcl_stats(ctypes.Structure):
     _fields_ = [
         ("kernel_launches", ctypes.c_longlong), ("dslash_launches", ctypes.c_longlong), ("dslash_ms", ctypes.c_double),
         ("dslash_timed", ctypes.c_longlong), ("dslash_bytes", ctypes.c_double), ("dslash_flops", ctypes.c_double),
+        ("prec_ms", ctypes.c_double * 5), ("prec_timed", ctypes.c_longlong * 5), ("prec_bytes", ctypes.c_double * 5),
+        ("prec_flops", ctypes.c_double * 5),
     ]
 
 
@@ -280,7 +283,11 @@ class Context:
     def wcl_get_stats(self, reset: bool = False) -> dict:
         s = wcl_stats()
         _check(load_library().wcl_get_stats(self.handle, ctypes.byref(s), int(reset)), "wcl_get_stats")
-        return {k: getattr(s, k) for k, _ in wcl_stats._fields_}
+        out = {}
+        for k, _ in wcl_stats._fields_:
+            v = getattr(s, k)
+            out[k] = list(v) if k.startswith("prec_") else v
+        return out
 
     def wcl_destroy(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -98,9 +98,11 @@ def test_gamma5_hermiticity_on_gpu(pkg):
 @pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((4, 4, 4, 4), 5), ((8, 4, 4, 6), 16)])
 def test_apply_Mpc_multi_rhs_f16(pkg, dims, nrhs, dagger, tensor_cores):
     """12-RHS 16-bit Schur operator: tensor-core (mma.sync f16, FP32 accumulate) and per-thread kernels."""
-    from paper_2411_08461_gb300.wcl import WCL_OPT_TENSOR_CORES
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS, WCL_OPT_TENSOR_CORES
 
     ctx, op, _ = _setup(pkg, dims, seed=13)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)  # the kernel under test, not the tuner's pick
+    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, 0)
     ctx.wcl_set_option(WCL_OPT_TENSOR_CORES, tensor_cores)
     psi = W.gaussian_fermion(dims, 14, nrhs=nrhs)[:, 0].copy()
     psi[1] *= 1e-7  # very different magnitudes per right-hand side
@@ -113,10 +115,12 @@ def test_apply_Mpc_multi_rhs_f16(pkg, dims, nrhs, dagger, tensor_cores):
 
 
 def test_tensor_core_and_per_thread_kernels_agree(pkg):
-    from paper_2411_08461_gb300.wcl import WCL_OPT_TENSOR_CORES
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS, WCL_OPT_TENSOR_CORES
 
     dims = (8, 8, 8, 16)
     ctx, _, _ = _setup(pkg, dims, seed=15)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, 0)
     psi = cuda(W.gaussian_fermion(dims, 16, nrhs=12)[:, 0].copy())
     outs = []
     for tc in (1, 0):
@@ -128,16 +132,19 @@ def test_tensor_core_and_per_thread_kernels_agree(pkg):
     ctx.close()
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("dagger", [False, True])
 @pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((2, 2, 2, 2), 16), ((8, 4, 4, 6), 7)])
-def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec):
-    """Multi-RHS Schur operator with links and clover staged in shared memory (16-site tiles,
-    ragged last tile for Vh = 96, 1296, 8, 384) against the oracle, RHS of very different size."""
-    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec, tile):
+    """Multi-RHS Schur operator with links and clover staged in shared memory (16- and 32-site
+    tiles, ragged last tile for Vh = 96, 1296, 8, 384) against the oracle, RHS of very different
+    size; FP64 always runs 16-site tiles."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
 
     ctx, op, _ = _setup(pkg, dims, seed=17)
-    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, 1)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, tile)
     psi = W.gaussian_fermion(dims, 18, nrhs=nrhs)[:, 0].copy()
     psi[1] *= 1e-7
     out = cuda(np.zeros_like(psi))
@@ -150,10 +157,11 @@ def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_shared_links_and_per_thread_kernels_agree(pkg, prec):
-    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
 
     dims = (8, 8, 8, 16)
     ctx, _, _ = _setup(pkg, dims, seed=19)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
     psi = cuda(W.gaussian_fermion(dims, 20, nrhs=12)[:, 0].copy())
     outs = []
     for sl in (1, 0):
@@ -164,3 +172,25 @@ def test_shared_links_and_per_thread_kernels_agree(pkg, prec):
     # same arithmetic in the same order: identical up to FMA contraction differences
     assert relerr(outs[0], outs[1]) <= (1e-14 if prec == "f64" else 1e-6)
     ctx.close()
+
+
+def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
+    """With the tuner on, the first apply of a configuration times the variants, writes the
+    choice to WCL_TUNE_CACHE, and the result still matches the oracle."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("WCL_TUNE_CACHE", str(cache))
+    dims = (6, 6, 4, 10)  # a shape no other test uses, so the choice is made here
+    ctx, op, _ = _setup(pkg, dims, seed=21)
+    psi = W.gaussian_fermion(dims, 22, nrhs=12)[:, 0].copy()
+    out = cuda(np.zeros_like(psi))
+    for _ in range(2):
+        ctx.wcl_apply_Mpc(out, cuda(psi), "f32", nrhs=12)
+    got = host(out)
+    for k in range(12):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], False)) <= TOL["f32"], k
+    ctx.close()
+    lines = [l.split() for l in cache.read_text().splitlines() if "6x6x4x10" in l]
+    assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
+    for v, b, ms, *_ in lines:
+        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 16), (1, 32)}
+        assert float(ms) > 0

@@ -97,17 +97,18 @@ def test_batch_of_uneven_lattices(pkg):
         c.close()
 
 
-@pytest.mark.parametrize("shared_links", [1, 0])
+@pytest.mark.parametrize("shared_links", [16, 32, 0])
 @pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
 def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
     """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials)."""
-    from paper_2411_08461_gb300.wcl import WCL_OPT_SHARED_LINKS
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
 
     shapes = [(4, 4, 4, 8), (6, 6, 2, 10)]
     ctxs, ops, bs, xs = [], [], [], []
     for k, dims in enumerate(shapes):
         g = W.gauge_links(dims, 0.3, 30 + k)
         c = pkg.Context(dims)
+        c.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
         c.wcl_set_option(WCL_OPT_SHARED_LINKS, shared_links)
         c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
         ctxs.append(c)
@@ -179,6 +180,7 @@ def test_twelve_rhs_f16_tensor_core_solve(pkg, solver):
     dims = (8, 8, 8, 16)
     gauge = W.gauge_links(dims, 0.3, 5)
     ctx = pkg.Context(dims)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_AUTOTUNE, 0)  # the tensor-core kernel, not the tuner's pick
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_TENSOR_CORES, 1)
     ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
     b = W.z2_fermion(dims, 6, nrhs=12)
