@@ -386,8 +386,8 @@ __device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void*
 }
 
 // r64 holds the operator result A_ee x_e - kappa D_eo x_o in precision Q and is
-// overwritten, in place, by the FP64 residual b_hat - (that); ro holds the odd
-// residual of the reconstruction (precision Q).
+// overwritten, in place, by the FP64 residual b_hat - (that); ro, when given,
+// holds the odd residual of the reconstruction (precision Q).
 template <int S, int Q>
 struct ResidualReplace {
   FieldRef r64, bhat, rS, rhat, ro;
@@ -395,8 +395,10 @@ struct ResidualReplace {
   __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
     using R = typename Traits<S>::R;
     cpx<double> y[12], b[12];
-    load_as_f64<Q>(b, rhs_ptr<Q>(ro, s.l, s.rhs, g.stride), g.stride, i);
-    acc[3] += norm_site(b);
+    if (ro.ptr[s.l]) {  // odd residual of the reconstruction (absent: x_o solves its rows exactly)
+      load_as_f64<Q>(b, rhs_ptr<Q>(ro, s.l, s.rhs, g.stride), g.stride, i);
+      acc[3] += norm_site(b);
+    }
     load_as_f64<Q>(y, rhs_ptr<Q>(r64, s.l, s.rhs, g.stride), g.stride, i);
     WCL_LD(F64, true, b, bhat);
     cpx<R> rs[12];

@@ -411,7 +411,7 @@ template <int TS>
 struct MrhsBounds;
 template <>
 struct MrhsBounds<16> {
-  static constexpr int THREADS = 256, MIN_BLOCKS = 3;
+  static constexpr int THREADS = 256, MIN_BLOCKS = 4;
 };
 template <>
 struct MrhsBounds<32> {
@@ -656,6 +656,7 @@ cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
       WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_PRE, EPI_NONE)                                     \
       WCL_DSLASH_CASE(P, true, MODE_XPAY | MODE_PRE, EPI_NONE)                                      \
       WCL_DSLASH_CASE(P, false, MODE_XPAY, EPI_NONE)                                                \
+      WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_POST, EPI_NONE)                                    \
       WCL_DSLASH_CASE(P, false, MODE_XPAY | MODE_POST | MODE_PRE | MODE_RECON, EPI_NONE)            \
       default: return cudaErrorInvalidValue;                                                        \
     }                                                                                               \

@@ -92,7 +92,19 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_quick(p, e);
 }
-__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+// a * b + c: the exact product of the high parts and its cross terms are added
+// to c with one two-sum and one final renormalisation (15 FP32 operations
+// instead of 18 for a product followed by a sum)
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  df_two_sum(p, c.hi, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  return df_quick(s, t);
+}
 // keep the floating-point fma visible next to the double-float one
 __host__ __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 __host__ __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }

@@ -223,12 +223,13 @@ struct KrylovSolver {
   wcl_status reliable_update(bool restart, int oprec, const int* mask) {
     const int bicg = (!cg && !restart) ? 1 : 0;
     if (oprec == DF64) {
-      // double-float operator on double-float copies; x_o, tmp64 and r64 hold
-      // double-float values until ResidualReplace turns r64 into the FP64 residual
+      // double-float operator on double-float copies; x_o and r64 hold double-float
+      // values until ResidualReplace turns r64 into the FP64 residual.  The odd
+      // residual of the reconstruction (rounding level) is left to the FP64 updates.
       WCL_CHECK(map(AddInto64Split<X>{x, xs, x_df}, mask));
-      WCL_CHECK(dslash_ex(ctxs, DF64, nrhs, x_o, x_df, &bo_df, &tmp64, 1, false, CL_AINV, CL_A, C_KAPPA, C_ONE, mask));
+      WCL_CHECK(dslash(ctxs, DF64, nrhs, x_o, x_df, &bo_df, 1, false, CL_AINV, CL_NONE, C_KAPPA, C_ONE, mask));
       WCL_CHECK(dslash(ctxs, DF64, nrhs, r64, x_o, &x_df, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, mask));
-      WCL_CHECK(reduce<4>(ResidualReplace<S, DF64>{r64, b_e, r, rhat, tmp64, bicg}, mask));
+      WCL_CHECK(reduce<4>(ResidualReplace<S, DF64>{r64, b_e, r, rhat, FieldRef{}, bicg}, mask));
       if (restart) WCL_CHECK(restart_krylov(mask));
       return WCL_OK;
     }
