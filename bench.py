@@ -54,9 +54,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairs", type=int, default=512, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
-    ap.add_argument("--case", default="solve", choices=["solve", "mhat", "compare"],
-                    help="mhat: only apply the Schur operator (the small case used for ncu captures)")
+    ap.add_argument("--case", default="solve", choices=["solve", "mhat", "compare", "batch", "throughput"],
+                    help="mhat: only apply the Schur operator (the small case used for ncu captures); "
+                         "batch: four uneven lattices x 12 Z2 sources in one batched solve vs single-RHS "
+                         "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
+    ap.add_argument("--dims", default="32,32,32,64", help="lattice of --case solve (the bench line uses 32^3x64)")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
     ap.add_argument("--prec", default="f32", choices=["f64", "df64", "f32", "f16", "bf16"], help="precision of --case mhat")
     ap.add_argument("--tensor-cores", type=int, default=0, help="--case mhat: 16-bit multi-RHS kernel on tensor cores")
@@ -224,9 +227,10 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     seed = SEED + rank  # replicas: every rank solves its own gauge field
-    gauge = W.gauge_links(DIMS, EPS, seed)
-    src = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
-    ctx = pkg.Context(DIMS, t_boundary=-1, device=local, stream=stream)
+    dims = tuple(int(v) for v in args.dims.split(","))
+    gauge = W.gauge_links(dims, EPS, seed)
+    src = np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])
+    ctx = pkg.Context(dims, t_boundary=-1, device=local, stream=stream)
     ctx.wcl_load_gauge(torch.from_numpy(gauge).to(dev), KAPPA, CSW)
     del gauge
     b = torch.from_numpy(src).to(dev)
@@ -286,7 +290,7 @@ def run_ours(args, rank, world, local):
     # FP32 fused dslash alone at 32^3x64 (two launches per M_hat), for the roofline target
     ctx.wcl_set_profiling(True)
     ctx.wcl_get_stats(reset=True)
-    pin = torch.from_numpy(W.gaussian_fermion(DIMS, 1)[0]).to(dev)
+    pin = torch.from_numpy(W.gaussian_fermion(dims, 1)[0]).to(dev)
     pout = torch.empty_like(pin)
     for _ in range(10):
         ctx.wcl_apply_Mpc(pout, pin, "f32")
@@ -305,7 +309,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{args.sloppy} storage / f32 arithmetic / f64 residual", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "nrhs": 12, "solver": "bicgstab even-odd",
+        "config": {"workload": WORKLOAD if dims == DIMS else WORKLOAD.replace("32^3x64", "x".join(map(str, dims))),
+                   "lattice": "x".join(map(str, dims)), "nrhs": 12, "solver": "bicgstab even-odd",
                    "sloppy": args.sloppy, "delta_reliable": args.delta, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set >> L2 (no flush needed)"},
         "solve": {"seconds": ms / 1e3, "iters_per_rhs": iters, "worst_true_residual": worst,
@@ -323,7 +328,8 @@ def run_ours(args, rank, world, local):
                         "peak_kind": "nominal", "frac": (d_flops / (d_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS) if d_ms > 0 else None,
                         "launches_timed": d_n, "ms_in_profiled_solve": d_ms},
         "dslash_f32": {"achieved": f32_gbs, "frac": (f32_gbs / peak) if f32_gbs else None, "unit": "GB/s",
-                       "launches": f32["dslash_timed"], "config": "32^3x64, 1 RHS, M_hat (864 + 960 B/site)"},
+                       "launches": f32["dslash_timed"],
+                       "config": "x".join(map(str, dims)) + ", 1 RHS, M_hat (864 + 960 B/site)"},
         "clocks": clk,
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": bh.numel() * 16,
                 "d2h_bytes_per_step": xh.numel() * 16, "ms_per_step": e2e_ms, "copied_back_matches": e2e_ok},
@@ -370,6 +376,141 @@ def run_mhat_case(args):
                       "tensor_cores": args.tensor_cores, "shared_links": args.shared_links,
                       "dslash_launches": st["dslash_timed"], "avg_launch_ms": st["dslash_ms"] / st["dslash_timed"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind}))
+    ctx.close()
+    return 0
+
+
+def _ctx_for(pkg, dims, seed, dev):
+    import torch
+
+    import workloads as W
+
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, seed)).to(dev), KAPPA, CSW)
+    return ctx
+
+
+def run_batch_case(args):
+    """Four uneven lattices, 12 Z2-noise sources each, to a 1e-10 true residual:
+    one batched, graph-captured wcl_invert_batch over all 48 systems, against one
+    12-RHS wcl_invert per lattice and against 12 single-RHS solves per lattice."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    shapes = [(8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 32), (24, 24, 24, 48)]
+    ctxs = [_ctx_for(pkg, d, 200 + k, dev) for k, d in enumerate(shapes)]
+    bs = [torch.from_numpy(W.z2_fermion(d, 300 + k, nrhs=12)).to(dev) for k, d in enumerate(shapes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=TOL, check_every=8,
+                                 delta_reliable=args.delta)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        out = None
+        for _ in range(args.steps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps / 1e3, out
+
+    def batched():
+        _, info = pkg.wcl_invert_batch(ctxs, xs, bs, 12, prm)
+        return info
+
+    t_batch, info_b = timed(batched)
+    res = {"case": "batch", "lattices": ["x".join(map(str, d)) for d in shapes], "sources": "12 Z2 per lattice",
+           "sloppy": args.sloppy, "tol": TOL,
+           "batched": {"seconds": t_batch, "worst_true_residual": max(i["true_residual"] for i in info_b),
+                       "iters_per_rhs": statistics.mean(i["iters"] for i in info_b)}}
+    t_multi, worst_m, t_single, worst_s = 0.0, 0.0, 0.0, 0.0
+    per = []
+    for k, (c, b, x) in enumerate(zip(ctxs, bs, xs)):
+        tm, info_m = timed(lambda: c.wcl_invert(x, b, 12, prm)[1])
+        worst_m = max(worst_m, max(i["true_residual"] for i in info_m))
+        x1 = torch.zeros_like(b[0])
+
+        def singles():
+            out = []
+            for r in range(12):
+                x1.zero_()
+                out += c.wcl_invert(x1, b[r].contiguous(), 1, prm)[1]
+            return out
+
+        ts, info_s = timed(singles)
+        worst_s = max(worst_s, max(i["true_residual"] for i in info_s))
+        t_multi += tm
+        t_single += ts
+        per.append({"lattice": res["lattices"][k], "twelve_rhs_s": tm, "single_rhs_x12_s": ts})
+    res["per_lattice_12rhs"] = {"seconds": t_multi, "worst_true_residual": worst_m}
+    res["single_rhs"] = {"seconds": t_single, "worst_true_residual": worst_s}
+    res["per_lattice"] = per
+    res["speedup_batched_vs_single"] = t_single / t_batch
+    res["speedup_batched_vs_per_lattice_12rhs"] = t_multi / t_batch
+    print(json.dumps(res))
+    for c in ctxs:
+        c.close()
+    return 0
+
+
+def run_throughput_case(args):
+    """16^3x32, FP32 fields and arithmetic: 100 applies of the full operator M
+    (two fused dslash+clover launches each, 10 warm-up) on Gaussian spinors, then
+    one BiCGStab solve from a point source to a 1e-10 true residual (FP32 inner
+    solver, FP64 reliable updates and true residual)."""
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    dims = (16, 16, 16, 32)
+    ctx = _ctx_for(pkg, dims, SEED, dev)
+    psi = torch.from_numpy(W.gaussian_fermion(dims, 1)).to(dev)
+    out = torch.empty_like(psi)
+    for _ in range(10):
+        ctx.wcl_apply_D(out, psi, "f32")
+    ctx.wcl_set_profiling(True)
+    ctx.wcl_get_stats(reset=True)
+    for _ in range(100):
+        ctx.wcl_apply_D(out, psi, "f32")
+    st = ctx.wcl_get_stats(reset=True)
+    ctx.wcl_set_profiling(False)
+    peak, kind = measured_peaks()
+    gbs = st["dslash_bytes"] / (st["dslash_ms"] * 1e-3) / 1e9
+    b = torch.from_numpy(W.point_source(dims, 0, 0)).to(dev)
+    x = torch.zeros_like(b)
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy="f32", tol=TOL, delta_reliable=args.delta)
+    ctx.wcl_invert(x, b, 1, prm)  # warm-up (tuning)
+    x.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, info = ctx.wcl_invert(x, b, 1, prm)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "throughput", "lattice": "16x16x16x32", "storage": "f32",
+                      "applies": 100, "fused_launches": st["dslash_timed"],
+                      "avg_launch_us": 1e3 * st["dslash_ms"] / st["dslash_timed"],
+                      "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind,
+                      "gflops": st["dslash_flops"] / (st["dslash_ms"] * 1e-3) / 1e9,
+                      "note": "the 16^3x32 FP32 working set (about 57 MB per launch) can stay in L2",
+                      "solve": {"seconds": e0.elapsed_time(e1) / 1e3, "iters": info[0]["iters"],
+                                "true_residual": info[0]["true_residual"],
+                                "reliable_updates": info[0]["reliable_updates"]}}))
     ctx.close()
     return 0
 
@@ -483,6 +624,10 @@ def main():
     args = parse()
     if args.case == "mhat":
         return run_mhat_case(args)
+    if args.case == "batch":
+        return run_batch_case(args)
+    if args.case == "throughput":
+        return run_throughput_case(args)
     if args.case == "compare":
         return run_compare_case(args)
     if args.impl == "reference":

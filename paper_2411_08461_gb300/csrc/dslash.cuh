@@ -341,39 +341,151 @@ struct CloverChunk<F16> : CloverChunk16<F16> {};
 template <>
 struct CloverChunk<BF16> : CloverChunk16<BF16> {};
 
-template <typename R, int TS>
-__device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[12], const R (*C)[TS], int ls) {
+// Per-site rows of reals in shared memory, read with 16-byte loads.  The row
+// length is padded so that eight consecutive sites' 16-byte reads fall in
+// distinct banks (row length in 4-byte words = 4 x odd, mod 32).
+template <typename R>
+struct SmemRow;
+template <>
+struct SmemRow<float> {
+  static constexpr int LINK = 20, CLOV = 76, PER = 4;
+  __device__ static void get(float* o, const float* row, int k) {
+    const float4 v = reinterpret_cast<const float4*>(row)[k];
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+template <>
+struct SmemRow<double> {
+  static constexpr int LINK = 18, CLOV = 74, PER = 2;
+  __device__ static void get(double* o, const double* row, int k) {
+    const double2 v = reinterpret_cast<const double2*>(row)[k];
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <typename R, int N>
+__device__ __forceinline__ void smem_read(R out[N], const R* row) {
+  constexpr int PER = SmemRow<R>::PER;
+  R t[(N + PER - 1) / PER * PER];
 #pragma unroll
-  for (int b = 0; b < 2; b++) {
-    R d[6];
-    cpx<R> L[15];
+  for (int k = 0; k < (N + PER - 1) / PER; k++) SmemRow<R>::get(t + PER * k, row, k);
 #pragma unroll
-    for (int k = 0; k < 6; k++) d[k] = C[36 * b + k][ls];
+  for (int k = 0; k < N; k++) out[k] = t[k];
+}
+
+// lower-triangle packing of a 6x6 block: entry k = r (r - 1) / 2 + c, c < r
+__host__ __device__ constexpr int tri_row(int k) { return k < 1 ? 1 : k < 3 ? 2 : k < 6 ? 3 : k < 10 ? 4 : 5; }
+__host__ __device__ constexpr int tri_col(int k) { return k - tri_row(k) * (tri_row(k) - 1) / 2; }
+
+// y = C x for one Hermitian 6x6 block streamed from its shared-memory row (6 diagonal
+// reals, then the 15 lower entries): each 16-byte read is consumed at once, in the
+// same order of operations as hermitian6_apply
+template <typename R>
+__device__ __forceinline__ void hermitian6_apply_row(cpx<R> y[6], const R* row, const cpx<R> x[6]) {
+  constexpr int PER = SmemRow<R>::PER;
 #pragma unroll
-    for (int k = 0; k < 15; k++) L[k] = {C[36 * b + 6 + 2 * k][ls], C[36 * b + 7 + 2 * k][ls]};
-    hermitian6_apply(y + 6 * b, d, L, x + 6 * b);
+  for (int q = 0; q < 36 / PER; q++) {
+    R v[PER];
+    SmemRow<R>::get(v, row, q);
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      const int e = q * PER + j;
+      if (e < 6) {
+        y[e] = v[j] * x[e];
+      } else if ((e - 6) % 2 == 0) {
+        const int k = (e - 6) / 2, r = tri_row(k), c = tri_col(k);
+        const cpx<R> l = {v[j], v[j + 1]};
+        cfma(y[r], l, x[c]);       // lower entry (r, c)
+        cfma_conj(y[c], l, x[r]);  // upper entry (c, r) = conj(l)
+      }
+    }
   }
 }
 
-template <int P, int MU, bool DAG, int TS>
+// y += beta C x for one block, streamed like hermitian6_apply_row (beta folded into
+// each entry, so no separate C x is held)
+template <typename R>
+__device__ __forceinline__ void hermitian6_axpy_row(cpx<R> y[6], R beta, const R* row, const cpx<R> x[6]) {
+  constexpr int PER = SmemRow<R>::PER;
+#pragma unroll
+  for (int q = 0; q < 36 / PER; q++) {
+    R v[PER];
+    SmemRow<R>::get(v, row, q);
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      const int e = q * PER + j;
+      if (e < 6) {
+        const R bd = beta * v[j];
+        y[e].re = fma(bd, x[e].re, y[e].re);
+        y[e].im = fma(bd, x[e].im, y[e].im);
+      } else if ((e - 6) % 2 == 0) {
+        const int k = (e - 6) / 2, r = tri_row(k), c = tri_col(k);
+        const cpx<R> l = {beta * v[j], beta * v[j + 1]};
+        cfma(y[r], l, x[c]);
+        cfma_conj(y[c], l, x[r]);
+      }
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void clover_apply_smem(cpx<R> y[12], const cpx<R> x[12], const R* row) {
+  hermitian6_apply_row(y, row, x);
+  hermitian6_apply_row(y + 6, row + 36, x + 6);
+}
+
+// o = sign U h (ADJ: sign U^+ h) for both spin halves of h, U streamed from its
+// shared-memory row (18 reals, row-major), in the order of link_mul
+template <bool ADJ, typename R>
+__device__ __forceinline__ void link_mul_row(const R* row, const cpx<R> h[6], cpx<R> o[6], R sign) {
+  constexpr int PER = SmemRow<R>::PER;
+#pragma unroll
+  for (int k = 0; k < 6; k++) o[k] = {R(0), R(0)};
+#pragma unroll
+  for (int q = 0; q < (18 + PER - 1) / PER; q++) {
+    R v[PER];
+    SmemRow<R>::get(v, row, q);
+#pragma unroll
+    for (int j = 0; j < PER; j += 2) {
+      const int e = (q * PER + j) / 2;
+      if (e < 9) {
+        const int a = e / 3, b = e % 3;
+        const cpx<R> u = {v[j], v[j + 1]};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          if (ADJ)
+            cfma_conj(o[3 * k + b], u, h[3 * k + a]);  // (U^+)_{ba} = conj(U_ab)
+          else
+            cfma(o[3 * k + a], u, h[3 * k + b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) o[k] = sign * o[k];
+}
+
+// U_f, U_b: shared-memory rows of the forward link at the site and the backward
+// link at the neighbour (18 reals each)
+template <int P, int MU, bool DAG>
 __device__ __forceinline__ void hop_dir_smem(cpx<typename Traits<P>::R> acc[12], const void* in, const float* in_norm,
-                                             long stride, long jf, long jb, const typename Traits<P>::R (*U)[18][TS],
-                                             int ls, typename Traits<P>::R sf, typename Traits<P>::R sb) {
+                                             long stride, long jf, long jb, const typename Traits<P>::R* U_f,
+                                             const typename Traits<P>::R* U_b, typename Traits<P>::R sf,
+                                             typename Traits<P>::R sb) {
   using R = typename Traits<P>::R;
   constexpr int SF = DAG ? +1 : -1;
   constexpr int SB = -SF;
-  cpx<R> psi[12], h[6], uh[6], u[3][3];
+  cpx<R> psi[12], h[6], uh[6];
   SpinorIO<P>::load(psi, in, in_norm, stride, jf);
-#pragma unroll
-  for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {U[2 * MU][2 * k][ls], U[2 * MU][2 * k + 1][ls]};
   project<MU, SF>(psi, h);
-  link_mul<false>(u, h, uh, sf);
+  link_mul_row<false>(U_f, h, uh, sf);
   reconstruct_acc<MU, SF>(acc, uh);
   SpinorIO<P>::load(psi, in, in_norm, stride, jb);
-#pragma unroll
-  for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {U[2 * MU + 1][2 * k][ls], U[2 * MU + 1][2 * k + 1][ls]};
   project<MU, SB>(psi, h);
-  link_mul<true>(u, h, uh, sb);
+  link_mul_row<true>(U_b, h, uh, sb);
   reconstruct_acc<MU, SB>(acc, uh);
 }
 
@@ -423,8 +535,9 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
     dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
   using R = typename Traits<P>::R;
   constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
-  __shared__ R Us[8][18][TS];             // links: 2 mu (fwd at the site), 2 mu + 1 (bwd at the neighbour)
-  __shared__ R Cs[CLOV ? 72 : 1][TS];     // unpacked clover, 72 reals per site
+  constexpr int LROW = SmemRow<R>::LINK, CROW = SmemRow<R>::CLOV;
+  __shared__ __align__(16) R Us[8][TS][LROW];  // links: 2 mu (fwd at the site), 2 mu + 1 (bwd at the neighbour)
+  __shared__ __align__(16) R Cs[CLOV ? TS : 1][CLOV ? CROW : 4];  // unpacked clover, 72 reals per site
   __shared__ int Nb[8][TS];               // neighbour indices within the other parity: 2 mu fwd, 2 mu + 1 bwd
   __shared__ unsigned char Tb[TS];        // bit 0: forward t hop wraps, bit 1: backward t hop wraps
   const Slice s = find_slice(a.b, blockIdx.x);  // one slice per lattice
@@ -465,8 +578,8 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
     }
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      Us[d][2 * k][ls] = u[k / 3][k % 3].re;
-      Us[d][2 * k + 1][ls] = u[k / 3][k % 3].im;
+      Us[d][ls][2 * k] = u[k / 3][k % 3].re;
+      Us[d][ls][2 * k + 1] = u[k / 3][k % 3].im;
     }
   }
   if (CLOV) {
@@ -484,7 +597,7 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
         for (int j = 0; j < CC::PER; j++) r[j] = R(0);
       }
 #pragma unroll
-      for (int j = 0; j < CC::PER; j++) Cs[CLOV ? CC::PER * k + j : 0][ls] = r[j];
+      for (int j = 0; j < CC::PER; j++) Cs[CLOV ? ls : 0][CLOV ? CC::PER * k + j : 0] = r[j];
     }
   }
   __syncthreads();
@@ -500,13 +613,13 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
-    hop_dir_smem<P, 0, DAG, TS>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us, ls, R(1), R(1));
-    hop_dir_smem<P, 1, DAG, TS>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us, ls, R(1), R(1));
-    hop_dir_smem<P, 2, DAG, TS>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us, ls, R(1), R(1));
+    hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us[0][ls], Us[1][ls], R(1), R(1));
+    hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us[2][ls], Us[3][ls], R(1), R(1));
+    hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us[4][ls], Us[5][ls], R(1), R(1));
     const int tb = Tb[ls];
     const R sf = (tb & 1) ? R(g.tb) : R(1);
     const R sb = (tb & 2) ? R(g.tb) : R(1);
-    hop_dir_smem<P, 3, DAG, TS>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us, ls, sf, sb);
+    hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us[6][ls], Us[7][ls], sf, sb);
     const R alpha = R(a.alpha[s.l]);
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
@@ -515,10 +628,8 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
       SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, rhs, stride), rhs_norm(a.x, s.l, rhs, stride), stride, i);
       const R beta = R(a.beta[s.l]);
       if (MODE & MODE_PRE) {
-        cpx<R> cx[12];
-        clover_apply_smem<R, TS>(cx, xv, Cs, ls);
-#pragma unroll
-        for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * cx[k];
+        hermitian6_axpy_row(acc, beta, Cs[CLOV ? ls : 0], xv);
+        hermitian6_axpy_row(acc + 6, beta, Cs[CLOV ? ls : 0] + 36, xv + 6);
       } else {
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
@@ -536,7 +647,7 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
     }
     if (MODE & MODE_POST) {
       cpx<R> y2[12];
-      clover_apply_smem<R, TS>(y2, acc, Cs, ls);
+      clover_apply_smem<R>(y2, acc, Cs[CLOV ? ls : 0]);
       SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
     } else {
       SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
