@@ -136,7 +136,13 @@ wcl_status wcl_create(wcl_ctx** out, const int dims[4], int t_boundary, int devi
  * 6x6 block in FP64 and stored in every precision. */
 wcl_status wcl_load_gauge(wcl_ctx* ctx, const void* d_gauge, double kappa, double csw);
 
-/* d_out = M d_in on the whole lattice for nrhs fields (QDP layout, complex128),
+/* Fermion buffers (d_in, d_out, d_x, d_b below) are device memory of the
+ * context's GPU, or page-locked host memory (cudaHostAlloc / cudaHostRegister),
+ * which the import and export kernels read and write in place through its device
+ * alias over the host link; anything else gives WCL_ERR_INVALID_ARG.  Work is
+ * ordered on the caller's stream: synchronise it before reading host outputs.
+ *
+ * d_out = M d_in on the whole lattice for nrhs fields (QDP layout, complex128),
  * computed in precision prec (links, clover and spinors stored in prec). */
 wcl_status wcl_apply_D(wcl_ctx* ctx, void* d_out, const void* d_in, wcl_prec prec, int nrhs);
 
@@ -146,7 +152,8 @@ wcl_status wcl_apply_D(wcl_ctx* ctx, void* d_out, const void* d_in, wcl_prec pre
 wcl_status wcl_apply_Mpc(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, wcl_prec prec, int nrhs, int dagger);
 
 /* Solve M x = b for nrhs right-hand sides (1..12) through the Schur complement.
- *   d_x, d_b: device, [nrhs][QDP fermion] complex128; d_x is written.
+ *   d_x, d_b: [nrhs][QDP fermion] complex128 (device or page-locked host);
+ *             d_x is written.
  *   info    : host array of nrhs entries, filled on return.
  * Returns WCL_OK when every right-hand side reached params->tol, otherwise the
  * first failing status (x still holds the best iterate). */

@@ -193,46 +193,89 @@ def _qdp_psi(psi_qdp, dims, c):
     return psi_qdp[(x + y + z + t) % 2, t, z, y, x // 2]
 
 
+def _hop_at(gauge_qdp, field, dims, s, t_boundary):
+    """(H psi)(s) at one site; field(c) returns the spinor [4][3] at coordinates c."""
+    lt = dims[3]
+    hop = np.zeros((4, 3), dtype=np.complex128)
+    for mu in range(4):
+        cf, cb = list(s), list(s)
+        cf[mu] += 1
+        cb[mu] -= 1
+        ef = t_boundary if (mu == 3 and s[3] == lt - 1) else 1.0
+        eb = t_boundary if (mu == 3 and s[3] == 0) else 1.0
+        uf = _qdp_link(gauge_qdp, dims, mu, s)
+        ub = _qdp_link(gauge_qdp, dims, mu, cb).conj().T
+        hop += ef * (ID4 - GAMMA[mu]) @ (field(tuple(cf)) @ uf.T)
+        hop += eb * (ID4 + GAMMA[mu]) @ (field(tuple(cb)) @ ub.T)
+    return hop
+
+
+def _clover_at(gauge_qdp, dims, s, kappa, csw):
+    """A(s) as a 12x12 matrix (index 3 spin + colour) from the four leaves at s."""
+    a = np.eye(12, dtype=np.complex128)
+    for mu, nu in PLANES:
+        def link(d, dm, dn):
+            c = list(s)
+            c[mu] += dm
+            c[nu] += dn
+            return _qdp_link(gauge_qdp, dims, d, c)
+        q = (link(mu, 0, 0) @ link(nu, 1, 0) @ link(mu, 0, 1).conj().T @ link(nu, 0, 0).conj().T
+             + link(nu, 0, 0) @ link(mu, -1, 1).conj().T @ link(nu, -1, 0).conj().T @ link(mu, -1, 0)
+             + link(mu, -1, 0).conj().T @ link(nu, -1, -1).conj().T @ link(mu, -1, -1) @ link(nu, 0, -1)
+             + link(nu, 0, -1).conj().T @ link(mu, 0, -1) @ link(nu, 1, -1) @ link(mu, 0, 0).conj().T)
+        f = (q - q.conj().T) / 8.0
+        f = f - np.trace(f) / 3.0 * np.eye(3)
+        a -= kappa * csw * np.kron(sigma(mu, nu), f)
+    return a
+
+
 def M_at_sites(gauge_qdp, psi_qdp, dims, kappa, csw, sites, t_boundary=-1):
     """(M psi)(s) for each s = (x, y, z, t) in `sites`, read straight from QDP arrays.
 
-    Same definition as WilsonClover.M (hopping term with the time-boundary sign,
-    clover term from the four leaves), evaluated one site at a time so that it
-    works on lattices of any size.  Pinned against WilsonClover.M.
+    Same definition as WilsonClover.M (Eq. 5: hopping term with the time-boundary
+    sign, clover term from the four leaves), evaluated one site at a time so that
+    it works on lattices of any size.  Pinned against WilsonClover.M.
     """
-    lx, ly, lz, lt = dims
     out = []
     for s in sites:
         s = tuple(int(v) for v in s)
+        hop = _hop_at(gauge_qdp, lambda c: _qdp_psi(psi_qdp, dims, c), dims, s, t_boundary)
+        a = _clover_at(gauge_qdp, dims, s, kappa, csw)
+        out.append((a @ _qdp_psi(psi_qdp, dims, s).reshape(12)).reshape(4, 3) - kappa * hop)
+    return np.array(out)
 
-        def shifted(c, mu, d):
-            c = list(c)
-            c[mu] += d
-            return tuple(c)
 
-        hop = np.zeros((4, 3), dtype=np.complex128)
-        for mu in range(4):
-            cf, cb = shifted(s, mu, 1), shifted(s, mu, -1)
-            ef = t_boundary if (mu == 3 and s[3] == lt - 1) else 1.0
-            eb = t_boundary if (mu == 3 and s[3] == 0) else 1.0
-            uf = _qdp_link(gauge_qdp, dims, mu, s)
-            ub = _qdp_link(gauge_qdp, dims, mu, cb).conj().T
-            hop += ef * (ID4 - GAMMA[mu]) @ (_qdp_psi(psi_qdp, dims, cf) @ uf.T)
-            hop += eb * (ID4 + GAMMA[mu]) @ (_qdp_psi(psi_qdp, dims, cb) @ ub.T)
-        a = np.eye(12, dtype=np.complex128)
-        for mu, nu in PLANES:
-            def link(d, dm, dn):
-                c = list(s)
-                c[mu] += dm
-                c[nu] += dn
-                return _qdp_link(gauge_qdp, dims, d, c)
-            q = (link(mu, 0, 0) @ link(nu, 1, 0) @ link(mu, 0, 1).conj().T @ link(nu, 0, 0).conj().T
-                 + link(nu, 0, 0) @ link(mu, -1, 1).conj().T @ link(nu, -1, 0).conj().T @ link(mu, -1, 0)
-                 + link(mu, -1, 0).conj().T @ link(nu, -1, -1).conj().T @ link(mu, -1, -1) @ link(nu, 0, -1)
-                 + link(nu, 0, -1).conj().T @ link(mu, 0, -1) @ link(nu, 1, -1) @ link(mu, 0, 0).conj().T)
-            f = (q - q.conj().T) / 8.0
-            f = f - np.trace(f) / 3.0 * np.eye(3)
-            a -= kappa * csw * np.kron(sigma(mu, nu), f)
-        val = (a @ _qdp_psi(psi_qdp, dims, s).reshape(12)).reshape(4, 3) - kappa * hop
-        out.append(val)
+def Mhat_at_sites(gauge_qdp, psi_even_qdp, dims, kappa, csw, sites, dagger=False, t_boundary=-1):
+    """(M_hat x_e)(s) for even sites s: A(s) x(s) - kappa^2 (D_eo A_oo^-1 D_oe x)(s),
+    the even-odd Schur complement of Eq. 5's operator on the even sublattice (§II.A
+    layout), one site at a time; M_hat^+ = gamma5 M_hat gamma5.  The odd-site
+    vectors A^-1 (D x)(n) are formed only at the neighbours of the sampled sites.
+    Pinned against WilsonClover.Mhat."""
+    lx, ly, lz, lt = dims
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)
+
+    def x_at(c):
+        x, y, z, t = (c[0] % lx, c[1] % ly, c[2] % lz, c[3] % lt)
+        if (x + y + z + t) % 2:
+            return np.zeros((4, 3), dtype=np.complex128)
+        v = psi_even_qdp[t, z, y, x // 2]
+        return g5 @ v if dagger else v
+
+    cache = {}
+
+    def y_at(c):
+        key = (c[0] % lx, c[1] % ly, c[2] % lz, c[3] % lt)
+        if key not in cache:
+            hop = _hop_at(gauge_qdp, x_at, dims, key, t_boundary)
+            a = _clover_at(gauge_qdp, dims, key, kappa, csw)
+            cache[key] = np.linalg.solve(a, hop.reshape(12)).reshape(4, 3)
+        return cache[key]
+
+    out = []
+    for s in sites:
+        s = tuple(int(v) for v in s)
+        assert sum(s) % 2 == 0, "M_hat lives on the even sites"
+        a = _clover_at(gauge_qdp, dims, s, kappa, csw)
+        val = (a @ x_at(s).reshape(12)).reshape(4, 3) - kappa * kappa * _hop_at(gauge_qdp, y_at, dims, s, t_boundary)
+        out.append(g5 @ val if dagger else val)
     return np.array(out)

@@ -3,6 +3,8 @@
 #include <cstring>
 #include <new>
 
+#include <vector>
+
 #include "context.cuh"
 
 namespace wcl {
@@ -43,6 +45,34 @@ wcl_status leave(wcl_ctx* c, wcl_status s) { return wcl_leave(c, s); }
 
 bool valid_prec(int p) { return p >= WCL_F64 && p <= WCL_BF16; }
 bool valid_apply_prec(int p) { return p >= WCL_F64 && p <= WCL_DF64; }
+
+// A fermion buffer of the caller: device memory of the context's device, or
+// page-locked host memory, which the import and export kernels read and write in
+// place through its device alias (over the host link, no staging copy).
+static bool field_ptr(const wcl_ctx* c, const void* p, const void** out, const char* what) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: not a CUDA-accessible pointer", what);
+    return false;
+  }
+  if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device) {
+    *out = p;
+    return true;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *out = at.devicePointer;
+    return true;
+  }
+  set_error("%s: neither device memory of the context's GPU nor page-locked host memory", what);
+  return false;
+}
+static bool field_ptr(const wcl_ctx* c, void* p, void** out, const char* what) {
+  const void* q = nullptr;
+  if (!field_ptr(c, static_cast<const void*>(p), &q, what)) return false;
+  *out = const_cast<void*>(q);
+  return true;
+}
 
 wcl_status alloc_lattice(wcl_ctx* c) {
   LatticeDevice& L = c->lat;
@@ -225,6 +255,8 @@ wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec,
     set_error("wcl_apply_D: invalid argument");
     return WCL_ERR_INVALID_ARG;
   }
+  if (!field_ptr(c, d_out, &d_out, "wcl_apply_D out") || !field_ptr(c, d_in, &d_in, "wcl_apply_D in"))
+    return WCL_ERR_INVALID_ARG;
   if (!c->lat.loaded) {
     set_error("wcl_apply_D: no gauge field loaded");
     return WCL_ERR_NO_GAUGE;
@@ -273,6 +305,8 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
     set_error("wcl_apply_Mpc: invalid argument");
     return WCL_ERR_INVALID_ARG;
   }
+  if (!field_ptr(c, d_out_e, &d_out_e, "wcl_apply_Mpc out") || !field_ptr(c, d_in_e, &d_in_e, "wcl_apply_Mpc in"))
+    return WCL_ERR_INVALID_ARG;
   if (!c->lat.loaded) {
     set_error("wcl_apply_Mpc: no gauge field loaded");
     return WCL_ERR_NO_GAUGE;
@@ -343,6 +377,8 @@ wcl_status wcl_invert(wcl_ctx* c, void* d_x, const void* d_b, int nrhs, const wc
     set_error("wcl_invert: no gauge field loaded");
     return WCL_ERR_NO_GAUGE;
   }
+  if (!field_ptr(c, d_x, &d_x, "wcl_invert x") || !field_ptr(c, d_b, &d_b, "wcl_invert b"))
+    return WCL_ERR_INVALID_ARG;
   WCL_CHECK(enter(c));
   std::vector<wcl_ctx*> v{c};
   void* xs[1] = {d_x};
@@ -379,6 +415,12 @@ wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, co
     }
     v.push_back(ctxs[i]);
   }
+  std::vector<void*> xs(nctx);
+  std::vector<const void*> bs(nctx);
+  for (int i = 0; i < nctx; i++)
+    if (!field_ptr(ctxs[i], d_x[i], &xs[i], "wcl_invert_batch x") ||
+        !field_ptr(ctxs[i], d_b[i], &bs[i], "wcl_invert_batch b"))
+      return WCL_ERR_INVALID_ARG;
   for (int i = 0; i < nctx; i++) {
     WCL_CHECK(enter(ctxs[i]));
     if (i) {
@@ -387,7 +429,7 @@ wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, co
       WCL_CUDA(cudaStreamWaitEvent(ctxs[0]->stream, ctxs[i]->ev_in, 0));
     }
   }
-  wcl_status s = solve(v, nrhs, params, d_x, d_b, info);
+  wcl_status s = solve(v, nrhs, params, xs.data(), bs.data(), info);
   return leave(ctxs[0], s);
 }
 

@@ -120,13 +120,13 @@ def _check(status: int, where: str):
         raise WclError(status, where, msg)
 
 
-def _ptr(t, dtype=None, numel=None, name="tensor"):
+def _ptr(t, dtype=None, numel=None, name="tensor", fermion=False):
     import torch
 
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
-    if not t.is_cuda:
-        raise ValueError(f"{name} must live on a CUDA device")
+    if not t.is_cuda and not (fermion and t.is_pinned()):
+        raise ValueError(f"{name} must live on a CUDA device" + (" or in pinned host memory" if fermion else ""))
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous (Sec. II.B: contiguous fields only)")
     if dtype is not None and t.dtype != dtype:
@@ -187,15 +187,15 @@ class Context:
         import torch
 
         n = self.fermion_numel * nrhs
-        _check(load_library().wcl_apply_D(self.handle, _ptr(out, torch.complex128, n, "out"),
-                                          _ptr(inp, torch.complex128, n, "in"), PREC[prec], nrhs), "wcl_apply_D")
+        _check(load_library().wcl_apply_D(self.handle, _ptr(out, torch.complex128, n, "out", True),
+                                          _ptr(inp, torch.complex128, n, "in", True), PREC[prec], nrhs), "wcl_apply_D")
 
     def wcl_apply_Mpc(self, out_e, in_e, prec: str = "f64", nrhs: int = 1, dagger: bool = False):
         import torch
 
         n = self.fermion_numel // 2 * nrhs
-        _check(load_library().wcl_apply_Mpc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
-                                            _ptr(in_e, torch.complex128, n, "in_e"), PREC[prec], nrhs, int(dagger)),
+        _check(load_library().wcl_apply_Mpc(self.handle, _ptr(out_e, torch.complex128, n, "out_e", True),
+                                            _ptr(in_e, torch.complex128, n, "in_e", True), PREC[prec], nrhs, int(dagger)),
                "wcl_apply_Mpc")
 
     def wcl_apply_Mpc_noalloc(self, out_e, in_e, dagger: bool = False):
@@ -213,7 +213,7 @@ class Context:
         params = params or wcl_default_params()
         info = (wcl_solve_info * nrhs)()
         n = self.fermion_numel * nrhs
-        st = load_library().wcl_invert(self.handle, _ptr(x, torch.complex128, n, "x"), _ptr(b, torch.complex128, n, "b"),
+        st = load_library().wcl_invert(self.handle, _ptr(x, torch.complex128, n, "x", True), _ptr(b, torch.complex128, n, "b", True),
                                        nrhs, ctypes.byref(params), info)
         if check:
             _check(st, "wcl_invert")
@@ -341,8 +341,8 @@ def wcl_invert_batch(ctxs: Sequence[Context], xs, bs, nrhs: int, params: wcl_sol
     params = params or wcl_default_params()
     n = len(ctxs)
     hs = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
-    xp = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, c.fermion_numel * nrhs, "x").value for c, x in zip(ctxs, xs)])
-    bp = (ctypes.c_void_p * n)(*[_ptr(b, torch.complex128, c.fermion_numel * nrhs, "b").value for c, b in zip(ctxs, bs)])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, c.fermion_numel * nrhs, "x", True).value for c, x in zip(ctxs, xs)])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b, torch.complex128, c.fermion_numel * nrhs, "b", True).value for c, b in zip(ctxs, bs)])
     info = (wcl_solve_info * (n * nrhs))()
     st = load_library().wcl_invert_batch(hs, n, xp, bp, nrhs, ctypes.byref(params), info)
     if check:

@@ -1,0 +1,81 @@
+"""Parity at the benchmark's full size, 32^3x64 with 12 right-hand sides, in the
+launch configuration the benchmark times (tuner on), checked on outputs the oracle
+evaluates one site at a time: sampled sites of M_hat x in FP32, FP16 and FP64, and
+the residual b - M x of a 12-source solve at sampled sites."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dirac
+
+from _gpu import TOL, built, cuda, host
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (32, 32, 32, 64)
+EPS, KAPPA, CSW = 0.3, 0.1235, 1.0
+
+
+@pytest.fixture(scope="module")
+def problem():
+    pkg = built()
+    gauge = W.gauge_links(DIMS, EPS, 0)
+    ctx = pkg.Context(DIMS)
+    ctx.wcl_load_gauge(cuda(gauge), KAPPA, CSW)
+    yield pkg, ctx, gauge
+    ctx.close()
+
+
+def even_sites(seed, n):
+    """Random even sites plus the corners of every wrap-around (x, y, z, t edges)."""
+    lx, ly, lz, lt = DIMS
+    fixed = [(0, 0, 0, 0), (lx - 1, 0, 0, 1), (1, ly - 1, 0, 0), (0, 1, lz - 1, 0), (0, 0, 1, lt - 1),
+             (lx - 1, ly - 1, lz - 1, lt - 1)]
+    rng = np.random.default_rng(seed)
+    out = list(fixed)
+    while len(out) < n:
+        s = tuple(int(rng.integers(0, d)) for d in DIMS)
+        if sum(s) % 2 == 0:
+            out.append(s)
+    return out
+
+
+def sampled(field_even, sites):
+    return np.array([field_even[t, z, y, x // 2] for x, y, z, t in sites])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "f64"])
+def test_schur_operator_12rhs_sampled(problem, prec):
+    pkg, ctx, gauge = problem
+    nrhs = 12
+    rng = np.random.default_rng(41)
+    shape = (nrhs, DIMS[3], DIMS[2], DIMS[1], DIMS[0] // 2, 4, 3)
+    psi = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    psi[3] *= 1e-6  # one RHS of a very different size
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs)
+    got = host(out)
+    sites = even_sites(42, 12)
+    for k in (0, 3, 7, 11):
+        ref = dirac.Mhat_at_sites(gauge, psi[k], DIMS, KAPPA, CSW, sites)
+        g = sampled(got[k], sites)
+        assert np.linalg.norm(g - ref) <= TOL[prec] * np.linalg.norm(ref), (prec, k)
+
+
+def test_twelve_source_solve_sampled_residual(problem):
+    """The bench's solve (FP32 inner solver, delta 3e-4, checks every 2 iterations):
+    every sampled site of b - M x is below 1e-10 ||b||, site 0 (the sources) included."""
+    pkg, ctx, gauge = problem
+    b = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
+    x = cuda(np.zeros_like(b))
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy="f32", tol=1e-10, check_every=2, delta_reliable=3e-4)
+    _, info = ctx.wcl_invert(x, cuda(b), 12, prm)
+    xh = host(x)
+    assert all(i["true_residual"] <= 1e-10 and i["status"] == 0 for i in info), info
+    sites = [(0, 0, 0, 0), (1, 0, 0, 0), (0, 0, 0, 1), (0, 0, 0, DIMS[3] - 1), (DIMS[0] - 1, 0, 0, 0),
+             (5, 7, 11, 13), (16, 16, 16, 32), (31, 30, 2, 40)]
+    for k in (0, 5, 11):
+        mx = dirac.M_at_sites(gauge, xh[k], DIMS, KAPPA, CSW, sites)
+        bs = np.array([b[k][(x0 + y + z + t) % 2, t, z, y, x0 // 2] for x0, y, z, t in sites])
+        res = np.abs(bs - mx).reshape(len(sites), -1).max(axis=1)
+        assert res.max() <= 1e-10 * np.linalg.norm(b[k]), (k, res)

@@ -192,3 +192,33 @@ def test_twelve_rhs_f16_tensor_core_solve(pkg, solver):
     for k in range(12):
         assert _oracle_true_residual(op, xh[k], b[k]) <= 1e-10, (k, info[k])
     ctx.close()
+
+
+def test_pinned_host_buffers(pkg):
+    """b and x in page-locked host memory give the same solution, bit for bit, as
+    device buffers; pageable host memory is refused."""
+    import torch
+
+    from paper_2411_08461_gb300.wcl import WclError
+
+    dims = (4, 4, 4, 8)
+    gauge = W.gauge_links(dims, 0.3, 3)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    b = W.z2_fermion(dims, 4, nrhs=2)
+    prm = pkg.wcl_default_params(sloppy="f32", tol=1e-10)
+    xd = cuda(np.zeros_like(b))
+    ctx.wcl_invert(xd, cuda(b), 2, prm)
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    _, info = ctx.wcl_invert(xh, bh, 2, prm)
+    torch.cuda.synchronize()
+    assert np.array_equal(xh.numpy(), host(xd))
+    yd, yh = cuda(np.zeros_like(b)), torch.zeros_like(bh).pin_memory()
+    ctx.wcl_apply_D(yd, xd, "f64", nrhs=2)
+    ctx.wcl_apply_D(yh, xh, "f64", nrhs=2)
+    torch.cuda.synchronize()
+    assert np.array_equal(yh.numpy(), host(yd))
+    with pytest.raises((WclError, ValueError)):
+        ctx.wcl_invert(torch.zeros_like(bh), torch.from_numpy(b.copy()), 2, prm)
+    ctx.close()

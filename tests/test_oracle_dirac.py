@@ -175,3 +175,20 @@ def test_site_by_site_evaluation_matches_whole_lattice():
     vals = dirac.M_at_sites(gq, psi_q, dims, 0.127, 1.3, sites)
     for (x, y, z, t), v in zip(sites, vals):
         np.testing.assert_allclose(v, full[t, z, y, x], atol=1e-13)
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_site_by_site_schur_operator_matches_whole_lattice(dagger):
+    """Mhat_at_sites (odd-site intermediates formed only where needed) equals the
+    whole-lattice M_hat, including wrap-around sites and the antiperiodic t hop."""
+    dims = (4, 2, 6, 4)
+    gq = W.gauge_links(dims, 0.6, 19)
+    xe = W.gaussian_fermion(dims, 20)[0]
+    op = dirac.from_qdp_problem(gq, dims, 0.127, 1.3)
+    full = np.zeros((2,) + xe.shape, dtype=np.complex128)
+    full[0] = xe
+    ref = op.Mhat(L.from_qdp(full, dims), dagger)
+    sites = [(0, 0, 0, 0), (3, 1, 0, 0), (1, 0, 5, 0), (2, 1, 5, 2), (0, 1, 2, 3), (3, 0, 2, 3)]
+    vals = dirac.Mhat_at_sites(gq, xe, dims, 0.127, 1.3, sites, dagger=dagger)
+    for (x, y, z, t), v in zip(sites, vals):
+        np.testing.assert_allclose(v, ref[t, z, y, x], atol=1e-13)
