@@ -300,11 +300,25 @@ def run_ours(args, rank, world, local):
     f32 = ctx.wcl_get_stats(reset=True)
     ctx.wcl_set_profiling(False)
 
+    # FP64 12-RHS operator alone (every RHS active), for its ALU roofline
+    ctx.wcl_set_profiling(True)
+    pin12 = torch.zeros((12,) + tuple(pin.shape), dtype=pin.dtype, device=dev)
+    pin12[:] = pin
+    pout12 = torch.empty_like(pin12)
+    ctx.wcl_apply_Mpc(pout12, pin12, "f64", nrhs=12)
+    ctx.wcl_get_stats(reset=True)
+    ctx.wcl_apply_Mpc(pout12, pin12, "f64", nrhs=12)
+    f64 = ctx.wcl_get_stats(reset=True)
+    ctx.wcl_set_profiling(False)
+    del pin12, pout12
+
     peak, peak_kind = measured_peaks()
     sp = PREC_INDEX[args.sloppy]
     s_ms, s_n, s_bytes, s_flops = st["prec_ms"][sp], st["prec_timed"][sp], st["prec_bytes"][sp], st["prec_flops"][sp]
     gbs = s_bytes / (s_ms * 1e-3) / 1e9 if s_ms > 0 else None
-    d_ms, d_n, d_flops = st["prec_ms"][0], st["prec_timed"][0], st["prec_flops"][0]
+    d_ms, d_n = st["prec_ms"][0], st["prec_timed"][0]
+    df_ms, df_n = st["prec_ms"][4], st["prec_timed"][4]
+    f64_gflops = f64["dslash_flops"] / (f64["dslash_ms"] * 1e-3) / 1e9 if f64["dslash_ms"] > 0 else None
     f32_gbs = f32["dslash_bytes"] / (f32["dslash_ms"] * 1e-3) / 1e9 if f32["dslash_ms"] > 0 else None
     traffic = os.environ.get("WCL_DSLASH_TRAFFIC")
     value = world * 1e3 / ms
@@ -326,10 +340,12 @@ def run_ours(args, rank, world, local):
                      "traffic": float(traffic) if traffic else None,
                      "gflops": s_flops / (s_ms * 1e-3) / 1e9 if s_ms > 0 else None,
                      "share_of_profiled_solve": s_ms / max(1e-9, pinfos[0]["seconds"] * 1e3)},
-        "fp64_dslash": {"bound": "alu", "kernel": "FP64 12-RHS dslash (source prep, reliable updates, true residual)",
-                        "gflops": d_flops / (d_ms * 1e-3) / 1e9 if d_ms > 0 else None, "peak_gflops": FP64_PEAK_GFLOPS,
-                        "peak_kind": "nominal", "frac": (d_flops / (d_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS) if d_ms > 0 else None,
-                        "launches_timed": d_n, "ms_in_profiled_solve": d_ms},
+        "fp64_dslash": {"bound": "alu", "kernel": "FP64 12-RHS fused dslash (final residual replacements)",
+                        "gflops": f64_gflops, "peak_gflops": FP64_PEAK_GFLOPS, "peak_kind": "nominal",
+                        "frac": (f64_gflops / FP64_PEAK_GFLOPS) if f64_gflops else None,
+                        "rate_measured_on": "M_hat, 12 RHS all active, 2 launches",
+                        "launches_in_profiled_solve": d_n, "ms_in_profiled_solve": d_ms,
+                        "double_float_launches_in_profiled_solve": df_n, "double_float_ms_in_profiled_solve": df_ms},
         "dslash_f32": {"achieved": f32_gbs, "frac": (f32_gbs / peak) if f32_gbs else None, "unit": "GB/s",
                        "launches": f32["dslash_timed"],
                        "config": "x".join(map(str, dims)) + ", 1 RHS, M_hat (864 + 960 B/site)"},

@@ -226,7 +226,7 @@ static wcl_status layer_both(const std::vector<wcl_ctx*>& ctxs, int nrhs, const 
   wcl_ctx* c0 = ctxs[0];
   PtcLayerArgs a;
   memset(&a, 0, sizeof a);
-  a.b = make_batch(ctxs, nrhs, 128, 0);
+  a.b = make_batch(ctxs, nrhs, ptc_layer_sites_per_cta(), 0);
   for (size_t l = 0; l < ctxs.size(); l++) {
     a.in[l] = in[l];
     a.out[l] = out[l];
@@ -241,7 +241,7 @@ static wcl_status layer_both(const std::vector<wcl_ctx*>& ctxs, int nrhs, const 
   for (int p = 0; p < 2; p++) {
     if (only_parity >= 0 && p != only_parity) continue;
     a.parity = p;
-    cudaError_t e = ptc_layer(a, 128, c0->stream);
+    cudaError_t e = ptc_layer(a, c0->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ptc layer launch");
     count_launch(c0);
   }

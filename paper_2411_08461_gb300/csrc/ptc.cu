@@ -74,77 +74,89 @@ __device__ __forceinline__ void transport(cpx<float> out[12], int s, const float
   }
 }
 
-template <int COUT>
+// One layer, four lanes per output site: lane q transports input channel q (if
+// q < cin) along each shift and accumulates output channel q (if q < cout); the
+// four transported spinors of a shift are exchanged by warp shuffles, so each
+// transport is computed once and a thread holds one accumulator, not four.
+// Weights live in shared memory with the output-channel stride padded by one
+// complex so that the four lanes' reads fall in different banks.
+constexpr int PTC_SITES_PER_CTA = 32;  // 128 threads
+constexpr int PTC_WSTRIDE = PTC_MAXC * PTC_NSHIFT * 16 + 1;
+
 __global__ void __launch_bounds__(128) ptc_layer_kernel(const __grid_constant__ PtcLayerArgs a) {
-  __shared__ float2 w_s[PTC_MAXC * PTC_MAXC * PTC_NSHIFT * 16];
-  const int nw = a.cout * a.cin * PTC_NSHIFT * 16;
-  for (int k = threadIdx.x; k < nw; k += blockDim.x) {
-    if (a.use_bf16) {
-      float2 v = __bfloat1622float2(a.wb[k]);
-      w_s[k] = v;
-    } else {
-      w_s[k] = a.w[k];
-    }
+  __shared__ float2 w_s[PTC_MAXC * PTC_WSTRIDE];
+  const int per_co = a.cin * PTC_NSHIFT * 16;
+  for (int k = threadIdx.x; k < a.cout * per_co; k += blockDim.x) {
+    const int co = k / per_co, r = k - co * per_co;
+    w_s[co * PTC_WSTRIDE + r] = a.use_bf16 ? __bfloat1622float2(a.wb[k]) : a.w[k];
   }
   __syncthreads();
   const Slice s = find_slice(a.b, blockIdx.x);
   const LatGeom& g = a.b.lat[s.l];
-  const long i = (long)s.chunk * blockDim.x + threadIdx.x;
-  if (i >= g.vh) return;
+  const int q = threadIdx.x & 3;
+  const long i = (long)s.chunk * PTC_SITES_PER_CTA + (threadIdx.x >> 2);
+  const bool site_ok = i < g.vh;  // lanes past the end still take part in the shuffles
+  const long ii = site_ok ? i : 0;
   const long stride = g.stride;
   const int p = a.parity;
-  const Nbr n = neighbours(g, p, i);
+  const Nbr n = neighbours(g, p, ii);
   const void* g_here = a.gauge[s.l][p];
   const void* g_there = a.gauge[s.l][1 - p];
+  const int qin = q < a.cin ? q : 0;
+  const float4* f_here = a.in[s.l] + ptc_field_offset(s.rhs, qin, a.cin, p, stride);
+  const float4* f_there = a.in[s.l] + ptc_field_offset(s.rhs, qin, a.cin, 1 - p, stride);
+  const float2* wq = w_s + (q < a.cout ? q : 0) * PTC_WSTRIDE;
+  const int lane0 = (threadIdx.x & 31) & ~3;
 
-  cpx<float> acc[COUT][12];
+  cpx<float> acc[12];
 #pragma unroll
-  for (int co = 0; co < COUT; co++)
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc[co][k] = {0.f, 0.f};
+  for (int k = 0; k < 12; k++) acc[k] = {0.f, 0.f};
 
-  for (int ci = 0; ci < a.cin; ci++) {
-    const float4* f_here = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, p, stride);
-    const float4* f_there = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, 1 - p, stride);
+#pragma unroll 1
+  for (int sh = 0; sh < PTC_NSHIFT; sh++) {
+    cpx<float> t[12];
+    if (q < a.cin) {
+      transport(t, sh, f_here, f_there, g_here, g_there, stride, ii, n);
+    } else {
 #pragma unroll
-    for (int sh = 0; sh < PTC_NSHIFT; sh++) {
-      cpx<float> t[12];
-      transport(t, sh, f_here, f_there, g_here, g_there, stride, i, n);
+      for (int k = 0; k < 12; k++) t[k] = {0.f, 0.f};
+    }
+#pragma unroll 1
+    for (int ci = 0; ci < a.cin; ci++) {
+      cpx<float> u[12];
 #pragma unroll
-      for (int co = 0; co < COUT; co++) {
-        const float2* w = w_s + ((co * a.cin + ci) * PTC_NSHIFT + sh) * 16;
-#pragma unroll
-        for (int al = 0; al < 4; al++)
-#pragma unroll
-          for (int be = 0; be < 4; be++) {
-            const float2 wv = w[al * 4 + be];
-            const cpx<float> wc = {wv.x, wv.y};
-#pragma unroll
-            for (int col = 0; col < 3; col++) cfma(acc[co][3 * al + col], wc, t[3 * be + col]);
-          }
+      for (int k = 0; k < 12; k++) {
+        u[k].re = __shfl_sync(0xffffffffu, t[k].re, lane0 + ci);
+        u[k].im = __shfl_sync(0xffffffffu, t[k].im, lane0 + ci);
       }
+      const float2* w = wq + (ci * PTC_NSHIFT + sh) * 16;
+#pragma unroll
+      for (int al = 0; al < 4; al++)
+#pragma unroll
+        for (int be = 0; be < 4; be++) {
+          const float2 wv = w[al * 4 + be];
+          const cpx<float> wc = {wv.x, wv.y};
+#pragma unroll
+          for (int col = 0; col < 3; col++) cfma(acc[3 * al + col], wc, u[3 * be + col]);
+        }
     }
   }
+  if (!site_ok || q >= a.cout) return;
+  float4* o = a.out[s.l] + ptc_field_offset(s.rhs, q, a.cout, p, stride);
+  if (a.accumulate) {
+    cpx<float> prev[12];
+    SpinorIO<F32>::load<false>(prev, o, nullptr, stride, i);
 #pragma unroll
-  for (int co = 0; co < COUT; co++) {
-    float4* o = a.out[s.l] + ptc_field_offset(s.rhs, co, COUT, p, stride);
-    if (a.accumulate) {
-      cpx<float> prev[12];
-      SpinorIO<F32>::load<false>(prev, o, nullptr, stride, i);
-#pragma unroll
-      for (int k = 0; k < 12; k++) acc[co][k] = acc[co][k] + prev[k];
-    }
-    SpinorIO<F32>::store(acc[co], o, nullptr, stride, i);
+    for (int k = 0; k < 12; k++) acc[k] = acc[k] + prev[k];
   }
+  SpinorIO<F32>::store(acc, o, nullptr, stride, i);
 }
 
-cudaError_t ptc_layer(const PtcLayerArgs& a, int block, cudaStream_t st) {
-  if (a.cout == 1)
-    ptc_layer_kernel<1><<<a.b.total_blocks, block, 0, st>>>(a);
-  else if (a.cout == 4)
-    ptc_layer_kernel<4><<<a.b.total_blocks, block, 0, st>>>(a);
-  else
-    return cudaErrorInvalidValue;
+int ptc_layer_sites_per_cta() { return PTC_SITES_PER_CTA; }
+
+cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st) {
+  if (a.cout < 1 || a.cout > PTC_MAXC || a.cin < 1 || a.cin > PTC_MAXC) return cudaErrorInvalidValue;
+  ptc_layer_kernel<<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a);
   return cudaGetLastError();
 }
 

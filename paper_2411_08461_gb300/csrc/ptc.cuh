@@ -48,7 +48,9 @@ __host__ __device__ inline size_t ptc_field_offset(int rhs, int c, int nch, int 
   return ((size_t)(rhs * nch + c) * 2 + parity) * 6 * (size_t)stride;
 }
 
-cudaError_t ptc_layer(const PtcLayerArgs& a, int block, cudaStream_t st);
+// a.b must be built with ptc_layer_sites_per_cta() sites per block
+cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st);
+int ptc_layer_sites_per_cta();
 
 // dW[co][ci][s] += sum_x G_co(x) (T_s in_ci)(x)^+  (colour summed), per slice;
 // writes per-block partials [slot][ci*9+s][chunk][co][16] as float2 (FP32)
