@@ -231,6 +231,11 @@ typedef enum {
                           every eligible kernel variant and launch shape and keeps the fastest
                           for the process; the environment variable WCL_TUNE_CACHE=<file>
                           makes the choices persist (text, appended).  0: fixed defaults */
+  ,
+  WCL_OPT_PTC_TENSOR_CORES = 4 /* 1 (default): the learned preconditioner's BF16 layers do the
+                                  channel and spin mixing on the tensor cores (mma.sync, BF16
+                                  weights, inputs split into three BF16 terms, FP32 accumulation);
+                                  0: FP32 SIMT mixing */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

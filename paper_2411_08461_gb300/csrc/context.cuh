@@ -59,6 +59,7 @@ struct wcl_ctx {
   int shared_links = 16;      // multi-RHS dslash with links/clover staged in shared memory:
                               // 0 off, else its sites per CTA when the tuner does not choose
   bool autotune = true;       // time the dslash variants of a new configuration on first use
+  bool ptc_tensor_cores = true;  // BF16 network layers mix channels on the tensor cores
   int blas_block = 256;
 };
 

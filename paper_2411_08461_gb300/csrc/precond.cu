@@ -238,10 +238,19 @@ static wcl_status layer_both(const std::vector<wcl_ctx*>& ctxs, int nrhs, const 
   a.cin = cin;
   a.cout = cout;
   a.use_bf16 = use_bf16;
+  uint4* frag = nullptr;
+  if (use_bf16 && c0->ptc_tensor_cores) {
+    void* q;
+    WCL_CHECK(ws_get(c0, "ptc_frag", sizeof(uint4) * ptc_frag_entries(PTC_MAXC, PTC_MAXC), &q));
+    frag = static_cast<uint4*>(q);
+    cudaError_t e = ptc_pack_frag(wb, cin, cout, frag, c0->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ptc fragment packing");
+    count_launch(c0);
+  }
   for (int p = 0; p < 2; p++) {
     if (only_parity >= 0 && p != only_parity) continue;
     a.parity = p;
-    cudaError_t e = ptc_layer(a, c0->stream);
+    cudaError_t e = ptc_layer(a, c0->stream, frag);
     if (e != cudaSuccess) return cuda_fail(e, "ptc layer launch");
     count_launch(c0);
   }

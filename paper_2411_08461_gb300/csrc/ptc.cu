@@ -154,9 +154,197 @@ __global__ void __launch_bounds__(128) ptc_layer_kernel(const __grid_constant__ 
 
 int ptc_layer_sites_per_cta() { return PTC_SITES_PER_CTA; }
 
-cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st) {
+// ---------------------------------------------------------------------------
+// Tensor-core layer (BF16 weights): the channel and spin mixing of every shift s
+// as a real GEMM on mma.sync.m16n8k16 (BF16 inputs, FP32 accumulation),
+//   C[(co, alpha, re/im)][site] += A_s[(co, alpha, re/im)][(ci, beta, re/im)] B_s[(ci, beta, re/im)][site],
+// one GEMM per colour.  A_s holds W[co][ci][s] in real form [[Re, -Im], [Im, Re]]
+// (exact: the weights are BF16).  B_s holds the transported inputs split into three
+// BF16 terms (hi + mid + lo carry 24 significant bits), so the sum matches the FP32
+// layer to FP32 rounding.  Lane (g, q) = (lane / 4, lane % 4): g is the site within
+// the warp's 8 sites; q is the input channel the lane transports, the spin beta of
+// the B values it holds and the output channel it stores.
+//
+// m16n8k16 fragments (g = lane / 4, t = lane % 4), k = ci_local * 8 + beta * 2 + re/im
+// within a k-step, m = co * 8 + alpha * 2 + re/im:
+//   A regs: (row g, k 2t..2t+1), (row g+8, k 2t..), (row g, k 2t+8..), (row g+8, k 2t+8..)
+//   B regs: (k 2t..2t+1, col g), (k 2t+8..2t+9, col g)
+//   C     : (row g, cols 2t, 2t+1), (row g+8, cols 2t, 2t+1)
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+// A fragments of one layer, [shift][mt][j][lane] (4 registers each)
+__global__ void ptc_pack_frag_kernel(const __nv_bfloat162* __restrict__ wb, int cin, int cout, int MT, int J,
+                                     uint4* __restrict__ frag) {
+  const int n = PTC_NSHIFT * MT * J * 32;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int lane = e & 31, j = (e >> 5) % J, mt = (e / (32 * J)) % MT, sh = e / (32 * J * MT);
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t r[4];
+  for (int reg = 0; reg < 4; reg++) {
+    const int row = 16 * mt + g + ((reg & 1) ? 8 : 0);
+    const int k0 = 16 * j + 2 * t + ((reg & 2) ? 8 : 0);
+    const int co = row >> 3, al = (row >> 1) & 3, ro = row & 1;
+    const int ci = k0 >> 3, be = (k0 >> 1) & 3;  // k0 even: re/im in = 0, 1
+    float lo = 0.f, hi = 0.f;
+    if (co < cout && ci < cin) {
+      const float2 w = __bfloat1622float2(wb[((co * cin + ci) * PTC_NSHIFT + sh) * 16 + al * 4 + be]);
+      // real form: row re: (Re, -Im); row im: (Im, Re)
+      lo = ro ? w.y : w.x;
+      hi = ro ? w.x : -w.y;
+    }
+    r[reg] = bf16x2_bits(__floats2bfloat162_rn(lo, hi));
+  }
+  frag[e] = make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// (re, im) -> three BF16 pairs whose sum is the FP32 pair to 24 bits
+__device__ __forceinline__ void split3(float2 v, uint32_t& h, uint32_t& m, uint32_t& l) {
+  const __nv_bfloat162 vh = __floats2bfloat162_rn(v.x, v.y);
+  const float2 fh = __bfloat1622float2(vh);
+  const float rx = v.x - fh.x, ry = v.y - fh.y;
+  const __nv_bfloat162 vm = __floats2bfloat162_rn(rx, ry);
+  const float2 fm = __bfloat1622float2(vm);
+  const __nv_bfloat162 vl = __floats2bfloat162_rn(rx - fm.x, ry - fm.y);
+  h = bf16x2_bits(vh);
+  m = bf16x2_bits(vm);
+  l = bf16x2_bits(vl);
+}
+
+constexpr int PTC_TROW = 4 * 12 + 1;  // staged complex per site (+1 against bank conflicts)
+
+template <int MT, int J>
+__global__ void __launch_bounds__(128) ptc_layer_tc_kernel(const __grid_constant__ PtcLayerArgs a,
+                                                           const uint4* __restrict__ frag) {
+  __shared__ uint4 a_s[PTC_NSHIFT * MT * J * 32];
+  __shared__ float2 t_s[4][8][PTC_TROW];
+  for (int k = threadIdx.x; k < PTC_NSHIFT * MT * J * 32; k += blockDim.x) a_s[k] = frag[k];
+  __syncthreads();
+  const Slice s = find_slice(a.b, blockIdx.x);
+  const LatGeom& g = a.b.lat[s.l];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gs = lane >> 2, q = lane & 3;
+  const long i = (long)s.chunk * PTC_SITES_PER_CTA + warp * 8 + gs;
+  const bool site_ok = i < g.vh;  // lanes past the end still take part in the MMAs
+  const long ii = site_ok ? i : 0;
+  const long stride = g.stride;
+  const int p = a.parity;
+  const Nbr n = neighbours(g, p, ii);
+  const void* g_here = a.gauge[s.l][p];
+  const void* g_there = a.gauge[s.l][1 - p];
+  const int qin = q < a.cin ? q : 0;
+  const float4* f_here = a.in[s.l] + ptc_field_offset(s.rhs, qin, a.cin, p, stride);
+  const float4* f_there = a.in[s.l] + ptc_field_offset(s.rhs, qin, a.cin, 1 - p, stride);
+  float2* my = t_s[warp][gs];
+
+  float acc[MT][3][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int r = 0; r < 4; r++) acc[mt][c][r] = 0.f;
+
+#pragma unroll 1
+  for (int sh = 0; sh < PTC_NSHIFT; sh++) {
+    cpx<float> t[12];
+    if (q < a.cin) {
+      transport(t, sh, f_here, f_there, g_here, g_there, stride, ii, n);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) t[k] = {0.f, 0.f};
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) my[q * 12 + k] = make_float2(t[k].re, t[k].im);
+    __syncwarp();
+    float2 v[2 * J][3];  // spin q of input channels 0 .. 2J-1, three colours
+#pragma unroll
+    for (int ci = 0; ci < 2 * J; ci++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) v[ci][c] = my[ci * 12 + q * 3 + c];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < J; j++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        uint32_t h0, m0, l0, h1, m1, l1;
+        split3(v[2 * j][c], h0, m0, l0);
+        split3(v[2 * j + 1][c], h1, m1, l1);
+#pragma unroll
+        for (int mt = 0; mt < MT; mt++) {
+          const uint4 af = a_s[((sh * MT + mt) * J + j) * 32 + lane];
+          mma_bf16(acc[mt][c], af, h0, h1);
+          mma_bf16(acc[mt][c], af, m0, m1);
+          mma_bf16(acc[mt][c], af, l0, l1);
+        }
+      }
+  }
+  // epilogue: C fragments -> [site][co * 12 + alpha * 3 + colour] -> one output channel per lane
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int row = 16 * mt + gs + ((r & 2) ? 8 : 0);
+        const int col = 2 * q + (r & 1);
+        const int co = row >> 3, al = (row >> 1) & 3;
+        float* dst = reinterpret_cast<float*>(&t_s[warp][col][co * 12 + al * 3 + c]);
+        dst[row & 1] = acc[mt][c][r];
+      }
+  __syncwarp();
+  if (!site_ok || q >= a.cout) return;
+  cpx<float> o12[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const float2 v2 = my[q * 12 + k];
+    o12[k] = {v2.x, v2.y};
+  }
+  float4* o = a.out[s.l] + ptc_field_offset(s.rhs, q, a.cout, p, stride);
+  if (a.accumulate) {
+    cpx<float> prev[12];
+    SpinorIO<F32>::load<false>(prev, o, nullptr, stride, i);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o12[k] = o12[k] + prev[k];
+  }
+  SpinorIO<F32>::store(o12, o, nullptr, stride, i);
+}
+
+int ptc_frag_entries(int cin, int cout) {
+  return PTC_NSHIFT * ((cout * 8 + 15) / 16) * ((cin * 8 + 15) / 16) * 32;
+}
+
+cudaError_t ptc_pack_frag(const __nv_bfloat162* wb, int cin, int cout, uint4* frag, cudaStream_t st) {
+  const int MT = (cout * 8 + 15) / 16, J = (cin * 8 + 15) / 16;
+  const int n = ptc_frag_entries(cin, cout);
+  ptc_pack_frag_kernel<<<(n + 127) / 128, 128, 0, st>>>(wb, cin, cout, MT, J, frag);
+  return cudaGetLastError();
+}
+
+cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st, const uint4* frag) {
   if (a.cout < 1 || a.cout > PTC_MAXC || a.cin < 1 || a.cin > PTC_MAXC) return cudaErrorInvalidValue;
-  ptc_layer_kernel<<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a);
+  if (frag && a.use_bf16) {
+    const int MT = (a.cout * 8 + 15) / 16, J = (a.cin * 8 + 15) / 16;
+    if (MT == 2 && J == 2)
+      ptc_layer_tc_kernel<2, 2><<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a, frag);
+    else if (MT == 2 && J == 1)
+      ptc_layer_tc_kernel<2, 1><<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a, frag);
+    else if (MT == 1 && J == 2)
+      ptc_layer_tc_kernel<1, 2><<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a, frag);
+    else
+      ptc_layer_tc_kernel<1, 1><<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a, frag);
+  } else {
+    ptc_layer_kernel<<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -48,9 +48,14 @@ __host__ __device__ inline size_t ptc_field_offset(int rhs, int c, int nch, int 
   return ((size_t)(rhs * nch + c) * 2 + parity) * 6 * (size_t)stride;
 }
 
-// a.b must be built with ptc_layer_sites_per_cta() sites per block
-cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st);
+// a.b must be built with ptc_layer_sites_per_cta() sites per block.  With frag
+// (the layer's packed A fragments, ptc_pack_frag) and a.use_bf16 the mixing runs on
+// the tensor cores; otherwise the FP32 SIMT layer.
+cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st, const uint4* frag = nullptr);
 int ptc_layer_sites_per_cta();
+// BF16 weights of one layer -> A fragments of the tensor-core layer (ptc_frag_entries uint4)
+int ptc_frag_entries(int cin, int cout);
+cudaError_t ptc_pack_frag(const __nv_bfloat162* wb, int cin, int cout, uint4* frag, cudaStream_t st);
 
 // dW[co][ci][s] += sum_x G_co(x) (T_s in_ci)(x)^+  (colour summed), per slice;
 // writes per-block partials [slot][ci*9+s][chunk][co][16] as float2 (FP32)

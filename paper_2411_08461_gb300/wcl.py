@@ -26,6 +26,7 @@ PTC_NWEIGHTS = 5760
 WCL_OPT_TENSOR_CORES = 1
 WCL_OPT_SHARED_LINKS = 2
 WCL_OPT_AUTOTUNE = 3
+WCL_OPT_PTC_TENSOR_CORES = 4
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 

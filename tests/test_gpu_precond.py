@@ -68,6 +68,28 @@ def test_forward_parity(pkg, bf16):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 2, 10)])
+def test_tensor_core_layers_match_simt(pkg, dims):
+    """BF16 network on the tensor cores (mma.sync, inputs split in three BF16 terms) equals
+    the FP32 SIMT layers with the same BF16 weights to FP32 accuracy; 6x4x2x10 leaves a
+    ragged last tile of sites."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_PTC_TENSOR_CORES
+
+    gauge = W.gauge_links(dims, 0.5, 31)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    ctx.wcl_precond_load(pkg.ptc_flatten(ptc.init_weights(seed=32, scale=0.3)))
+    r = cuda(W.gaussian_fermion(dims, 33, nrhs=3)[:, 0].copy())
+    outs = []
+    for tc in (1, 0):
+        ctx.wcl_set_option(WCL_OPT_PTC_TENSOR_CORES, tc)
+        z = cuda(np.zeros(r.shape, dtype=np.complex128))
+        ctx.wcl_precond_apply(z, r, 3, bf16=True)
+        outs.append(host(z))
+    assert relerr(outs[0], outs[1]) <= 1e-5  # the FP32 tolerance
+    ctx.close()
+
+
 def test_loss_and_gradient_parity(pkg):
     dims = (4, 4, 2, 4)
     gauge = W.gauge_links(dims, 0.5, 7)
