@@ -273,7 +273,10 @@ __global__ void __launch_bounds__(128) ptc_layer_tc_kernel(const __grid_constant
       for (int c = 0; c < 3; c++) v[ci][c] = my[ci * 12 + q * 3 + c];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < J; j++)
+    for (int j = 0; j < J; j++) {
+      uint4 af[MT];
+#pragma unroll
+      for (int mt = 0; mt < MT; mt++) af[mt] = a_s[((sh * MT + mt) * J + j) * 32 + lane];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         uint32_t h0, m0, l0, h1, m1, l1;
@@ -281,12 +284,12 @@ __global__ void __launch_bounds__(128) ptc_layer_tc_kernel(const __grid_constant
         split3(v[2 * j + 1][c], h1, m1, l1);
 #pragma unroll
         for (int mt = 0; mt < MT; mt++) {
-          const uint4 af = a_s[((sh * MT + mt) * J + j) * 32 + lane];
-          mma_bf16(acc[mt][c], af, h0, h1);
-          mma_bf16(acc[mt][c], af, m0, m1);
-          mma_bf16(acc[mt][c], af, l0, l1);
+          mma_bf16(acc[mt][c], af[mt], h0, h1);
+          mma_bf16(acc[mt][c], af[mt], m0, m1);
+          mma_bf16(acc[mt][c], af[mt], l0, l1);
         }
       }
+    }
   }
   // epilogue: C fragments -> [site][co * 12 + alpha * 3 + colour] -> one output channel per lane
 #pragma unroll
