@@ -90,7 +90,10 @@ typedef enum {
 
 typedef struct {
   wcl_solver solver;
-  wcl_prec outer;        /* must be WCL_F64: solution and true residual are FP64 */
+  wcl_prec outer;        /* residual replacements of a mixed-precision solve: WCL_DF64 (default)
+                            runs the intermediate ones with the double-float operator and the
+                            final ones in IEEE FP64; WCL_F64 runs all of them in FP64.  The
+                            solution, the reductions and every reported residual are FP64. */
   wcl_prec sloppy;       /* precision of the inner Krylov vectors, links and clover */
   double tol;            /* target relative true residual ||b - M x|| / ||b|| */
   int maxiter;           /* total inner iterations per right-hand side */
@@ -104,12 +107,12 @@ typedef struct {
 typedef struct {
   int iters;             /* inner iterations */
   double true_residual;  /* ||b - M x|| / ||b|| in FP64 over the whole lattice */
-  int reliable_updates;  /* FP64 residual replacements */
+  int reliable_updates;  /* residual replacements (double-float or FP64) */
   int status;            /* wcl_status of this right-hand side */
   double seconds;        /* wall time of the whole call */
 } wcl_solve_info;
 
-/* Fill *p with defaults: BiCGStab, outer F64, sloppy F32, tol 1e-10,
+/* Fill *p with defaults: BiCGStab, outer DF64, sloppy F32, tol 1e-10,
  * maxiter 20000, delta 0.1, no restarts, nkrylov 20, graphs on, check_every 8. */
 void wcl_default_params(wcl_solve_params* p);
 

@@ -114,7 +114,7 @@ void wcl_default_params(wcl_solve_params* p) {
   if (!p) return;
   memset(p, 0, sizeof(*p));
   p->solver = WCL_BICGSTAB;
-  p->outer = WCL_F64;
+  p->outer = WCL_DF64;
   p->sloppy = WCL_F32;
   p->tol = 1e-10;
   p->maxiter = 20000;
@@ -339,9 +339,10 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
 }
 
 static wcl_status check_params(const wcl_solve_params* p) {
-  if (!p || p->outer != WCL_F64 || !valid_prec(p->sloppy) || !(p->tol > 0) || p->maxiter < 1 ||
+  if (!p || (p->outer != WCL_F64 && p->outer != WCL_DF64) || !valid_prec(p->sloppy) || !(p->tol > 0) ||
+      p->maxiter < 1 ||
       !(p->delta_reliable > 0 && p->delta_reliable < 1) || p->check_every < 1 || p->check_every > 1024) {
-    set_error("invalid solve parameters (outer must be F64, 0 < delta < 1, tol > 0)");
+    set_error("invalid solve parameters (outer F64 or DF64, 0 < delta < 1, tol > 0)");
     return WCL_ERR_INVALID_ARG;
   }
   if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED && p->solver != WCL_GCR) {

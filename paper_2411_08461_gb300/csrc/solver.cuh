@@ -457,7 +457,7 @@ struct KrylovSolver {
     bb = make_batch(ctxs, nrhs, blk, RED_MAXCH);
     // Intermediate residual replacements of a mixed-precision solve use the
     // double-float operator (FP32 pipes); every final one is IEEE FP64.
-    use_df = S != F64;
+    use_df = S != F64 && prm.outer == WCL_DF64;
     WCL_CHECK(alloc());
     stop2.assign(nslot, 0);
     r2max.assign(nslot, 0);

@@ -44,7 +44,7 @@ def test_host_only_calls_without_a_gpu():
 
     lib = wcl.load_library()
     p = wcl.wcl_default_params()
-    assert p.outer == 0 and p.tol == 1e-10 and p.gcr_nkrylov == 20
+    assert p.outer == 4 and p.tol == 1e-10 and p.gcr_nkrylov == 20  # double-float replacements, FP64 final
     assert lib.wcl_status_string(4) == b"not converged"
     tp = wcl.wcl_default_train_params()
     assert tp.epochs == 4 and tp.batch == 8

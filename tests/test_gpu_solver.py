@@ -43,16 +43,19 @@ def test_plain_fp64_point_source(pkg, solver, graphs):
     ctx.close()
 
 
+@pytest.mark.parametrize("outer", ["df64", "f64"])
 @pytest.mark.parametrize("sloppy", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
-def test_mixed_precision_reaches_1e10(pkg, sloppy, solver):
+def test_mixed_precision_reaches_1e10(pkg, sloppy, solver, outer):
+    """Inner FP32/FP16/BF16 solver; residual replacements double-float then FP64, or all FP64."""
     dims = (8, 8, 8, 16)
     gauge = W.gauge_links(dims, 0.3, 0)
     ctx = pkg.Context(dims)
     ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
     b = W.gaussian_fermion(dims, 1)
     x = cuda(np.zeros_like(b))
-    _, info = ctx.wcl_invert(x, cuda(b), 1, pkg.wcl_default_params(solver=solver, sloppy=sloppy, tol=1e-10))
+    _, info = ctx.wcl_invert(x, cuda(b), 1, pkg.wcl_default_params(solver=solver, sloppy=sloppy, tol=1e-10,
+                                                                   outer=outer))
     op = dirac.from_qdp_problem(gauge, dims, 0.1235, 1.0)
     tr = _oracle_true_residual(op, host(x), b)
     assert tr <= 1e-10, (tr, info)
