@@ -156,7 +156,7 @@ class WilsonClover:
         return xe + xo
 
     def true_residual(self, x, b) -> float:
-        """||b - M x||_2 / ||b||_2 over the whole lattice (the judged quantity)."""
+        """||b - M x||_2 / ||b||_2 over the whole lattice: the relative true residual of the full system."""
         return float(np.linalg.norm(b - self.M(x)) / np.linalg.norm(b))
 
 
