@@ -223,7 +223,7 @@ typedef enum {
                               multiplies on the tensor cores (mma.sync, FP32 accumulation);
                               0 (default): the per-thread kernel, faster with this field layout */
   ,
-  WCL_OPT_SHARED_LINKS = 2 /* 1 (default) or 16 or 32: the multi-RHS dslash (4..16 RHS, Schur
+  WCL_OPT_SHARED_LINKS = 2 /* 1 (default) or 8, 16, 32: the multi-RHS dslash (4..16 RHS, Schur
                               operator) may stage the links and clover of a tile of sites in shared
                               memory once for all RHS; the value is the tile (1 = 16 sites) used
                               when the autotuner is off (FP64 always uses 16).

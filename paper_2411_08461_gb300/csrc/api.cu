@@ -439,7 +439,7 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
   switch (option) {
     case WCL_OPT_TENSOR_CORES: c->tensor_cores = value != 0; return WCL_OK;
     case WCL_OPT_SHARED_LINKS:
-      if (value == 0 || value == 1 || value == 16 || value == 32) {
+      if (value == 0 || value == 1 || value == 8 || value == 16 || value == 32) {
         c->shared_links = value == 1 ? 16 : value;
         return WCL_OK;
       }

@@ -195,6 +195,7 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   std::vector<TuneChoice> cand;
   for (int blk : {64, 128, 256, 512}) cand.push_back({V_THREAD, blk});
   if (mr_ok) {
+    cand.push_back({V_SMEM, 8});
     cand.push_back({V_SMEM, 16});
     if (prec != F64) cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
   }

@@ -289,13 +289,13 @@ __global__ void __launch_bounds__(256) clover_kernel(const __grid_constant__ Clo
 }
 
 // ---------------------------------------------------------------------------
-// Multi-RHS kernel: a CTA covers TS (16 or 32) consecutive output sites and every
+// Multi-RHS kernel: a CTA covers TS (8, 16 or 32) consecutive output sites and every
 // right-hand side.  Links and clover of the tile are read from memory once,
 // unpacked (12-real reconstruction, 16-bit scaling) into shared memory, and
 // reused by all RHS, as are the neighbour indices; each thread then computes one
 // (site, rhs) pair.  The TS threads of one RHS are consecutive lanes of a warp.  Fused reductions write one partial per (RHS,
 // CTA) and are finalised by tc_epi_finalize_kernel.
-constexpr int MR_SITES = 16;  // smallest tile (sizes the reduction partials)
+constexpr int MR_SITES = 8;  // smallest tile (sizes the reduction partials)
 
 // Unpack chunk k of the packed clover term of site i into reals r[0..n) (n per chunk:
 // 2 for FP64, 4 for FP32, 8 for the 16-bit formats, which carry one scale per site).
@@ -517,10 +517,15 @@ __device__ __forceinline__ SiteNbr site_neighbours(const LatGeom& g, int p, long
   return n;
 }
 
-// Register cap: 16-site tiles (up to 256 threads) keep three CTAs per SM; 32-site
-// tiles (up to 512 threads) keep one CTA's registers within half the file for 12 RHS.
+// Register cap: 8- and 16-site tiles keep 64 registers per thread (five 192-thread
+// or ten 96-thread CTAs per SM for 12 RHS); 32-site tiles (up to 512 threads) are
+// capped at 128.
 template <int TS>
 struct MrhsBounds;
+template <>
+struct MrhsBounds<8> {
+  static constexpr int THREADS = 128, MIN_BLOCKS = 8;
+};
 template <>
 struct MrhsBounds<16> {
   static constexpr int THREADS = 256, MIN_BLOCKS = 4;
@@ -723,12 +728,14 @@ cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int t
   case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                                \
     if (ts == 32)                                                                               \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 32><<<a.b.total_blocks, threads, 0, st>>>(a);       \
+    else if (ts == 8)                                                                           \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 8><<<a.b.total_blocks, threads, 0, st>>>(a);        \
     else                                                                                        \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 16><<<a.b.total_blocks, threads, 0, st>>>(a);       \
     fin = EPI;                                                                                  \
     break;
 
-// ts: sites per CTA (16 or 32); the geometry a.b must have been built with that tile
+// ts: sites per CTA (8, 16 or 32); the geometry a.b must have been built with that tile
 #define WCL_DEFINE_MRHS_LAUNCHER(P)                                                              \
   template <>                                                                                    \
   cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st) { \

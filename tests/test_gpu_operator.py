@@ -132,12 +132,12 @@ def test_tensor_core_and_per_thread_kernels_agree(pkg):
     ctx.close()
 
 
-@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("dagger", [False, True])
 @pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((2, 2, 2, 2), 16), ((8, 4, 4, 6), 7)])
 def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec, tile):
-    """Multi-RHS Schur operator with links and clover staged in shared memory (16- and 32-site
+    """Multi-RHS Schur operator with links and clover staged in shared memory (8-, 16- and 32-site
     tiles, ragged last tile for Vh = 96, 1296, 8, 384) against the oracle, RHS of very different
     size; FP64 always runs 16-site tiles."""
     from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
@@ -192,5 +192,5 @@ def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
     lines = [l.split() for l in cache.read_text().splitlines() if "6x6x4x10" in l]
     assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
     for v, b, ms, *_ in lines:
-        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 16), (1, 32)}
+        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32)}
         assert float(ms) > 0

@@ -100,7 +100,7 @@ def test_batch_of_uneven_lattices(pkg):
         c.close()
 
 
-@pytest.mark.parametrize("shared_links", [16, 32, 0])
+@pytest.mark.parametrize("shared_links", [8, 16, 32, 0])
 @pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
 def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
     """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials)."""
