@@ -298,33 +298,57 @@ __global__ void clover_pack_kernel(const double2* __restrict__ src, long st, lon
 // ---------------------------------------------------------------------------
 // fermion import / export between QDP complex128 and internal F64 parity fields.
 //   src element (rhs, i, k) at src + rhs*rhs_stride + par_off + i*12 + k
-__global__ void fermion_import_kernel(const double2* __restrict__ src, long rhs_stride, long par_off, long vh, int nrhs,
-                                      double2* __restrict__ dst, long st, int* __restrict__ flags) {
-  const long n = (long)nrhs * vh;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / vh);
-    const long i = idx % vh;
-    const double2* s = src + r * rhs_stride + par_off + i * 12;
-    double2* d = dst + (long)r * 12 * st;
-    bool fin = true;
-    for (int k = 0; k < 12; k++) {
-      double2 v = s[k];
+// QDP fermion (12 complexes per site, site-major) <-> internal chunk-major layout,
+// through a shared-memory tile of 32 sites so that both the QDP side (which may be
+// page-locked host memory read over the host link) and the chunk side move in
+// contiguous runs: the QDP run of a tile is 32 x 12 consecutive complexes.
+constexpr int FIO_SITES = 32;
+
+__global__ void __launch_bounds__(128) fermion_import_kernel(const double2* __restrict__ src, long rhs_stride,
+                                                             long par_off, long vh, int nrhs, double2* __restrict__ dst,
+                                                             long st, int* __restrict__ flags) {
+  __shared__ double2 tile[12][FIO_SITES + 1];
+  const long ntile = (vh + FIO_SITES - 1) / FIO_SITES;
+  bool fin = true;
+  for (long tix = blockIdx.x; tix < (long)nrhs * ntile; tix += gridDim.x) {
+    const int r = (int)(tix / ntile);
+    const long i0 = (tix % ntile) * FIO_SITES;
+    const int ns = (int)((vh - i0) < FIO_SITES ? (vh - i0) : FIO_SITES);
+    const double2* s = src + r * rhs_stride + par_off + i0 * 12;
+    for (int e = threadIdx.x; e < ns * 12; e += blockDim.x) {
+      const double2 v = s[e];
       fin = fin && isfinite(v.x) && isfinite(v.y);
-      d[k * st + i] = v;
+      tile[e % 12][e / 12] = v;
     }
-    if (!fin && flags) atomicOr(flags, 1);
+    __syncthreads();
+    double2* d = dst + (long)r * 12 * st + i0;
+    for (int e = threadIdx.x; e < 12 * FIO_SITES; e += blockDim.x) {
+      const int k = e / FIO_SITES, site = e % FIO_SITES;
+      if (site < ns) d[k * st + site] = tile[k][site];
+    }
+    __syncthreads();
   }
+  if (!fin && flags) atomicOr(flags, 1);
 }
 
-__global__ void fermion_export_kernel(const double2* __restrict__ src, long st, long vh, int nrhs, double2* __restrict__ dst,
-                                      long rhs_stride, long par_off) {
-  const long n = (long)nrhs * vh;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / vh);
-    const long i = idx % vh;
-    const double2* s = src + (long)r * 12 * st;
-    double2* d = dst + r * rhs_stride + par_off + i * 12;
-    for (int k = 0; k < 12; k++) d[k] = s[k * st + i];
+__global__ void __launch_bounds__(128) fermion_export_kernel(const double2* __restrict__ src, long st, long vh,
+                                                             int nrhs, double2* __restrict__ dst, long rhs_stride,
+                                                             long par_off) {
+  __shared__ double2 tile[12][FIO_SITES + 1];
+  const long ntile = (vh + FIO_SITES - 1) / FIO_SITES;
+  for (long tix = blockIdx.x; tix < (long)nrhs * ntile; tix += gridDim.x) {
+    const int r = (int)(tix / ntile);
+    const long i0 = (tix % ntile) * FIO_SITES;
+    const int ns = (int)((vh - i0) < FIO_SITES ? (vh - i0) : FIO_SITES);
+    const double2* s = src + (long)r * 12 * st + i0;
+    for (int e = threadIdx.x; e < 12 * FIO_SITES; e += blockDim.x) {
+      const int k = e / FIO_SITES, site = e % FIO_SITES;
+      if (site < ns) tile[k][site] = s[k * st + site];
+    }
+    __syncthreads();
+    double2* d = dst + r * rhs_stride + par_off + i0 * 12;
+    for (int e = threadIdx.x; e < ns * 12; e += blockDim.x) d[e] = tile[e % 12][e / 12];
+    __syncthreads();
   }
 }
 
@@ -405,7 +429,7 @@ cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa
 
 cudaError_t import_fermion(const LatticeDevice& L, const void* d_src, long rhs_stride_c, long par_off_c, int nrhs,
                            void* d_dst64, int* d_flags, cudaStream_t st) {
-  fermion_import_kernel<<<grid_for((long)nrhs * L.vh, 256), 256, 0, st>>>(
+  fermion_import_kernel<<<grid_for((long)nrhs * ((L.vh + FIO_SITES - 1) / FIO_SITES), 1), 128, 0, st>>>(
       static_cast<const double2*>(d_src), rhs_stride_c, par_off_c, L.vh, nrhs, static_cast<double2*>(d_dst64), L.stride,
       d_flags);
   return cudaGetLastError();
@@ -413,7 +437,7 @@ cudaError_t import_fermion(const LatticeDevice& L, const void* d_src, long rhs_s
 
 cudaError_t export_fermion(const LatticeDevice& L, const void* d_src64, int nrhs, void* d_dst, long rhs_stride_c,
                            long par_off_c, cudaStream_t st) {
-  fermion_export_kernel<<<grid_for((long)nrhs * L.vh, 256), 256, 0, st>>>(
+  fermion_export_kernel<<<grid_for((long)nrhs * ((L.vh + FIO_SITES - 1) / FIO_SITES), 1), 128, 0, st>>>(
       static_cast<const double2*>(d_src64), L.stride, L.vh, nrhs, static_cast<double2*>(d_dst), rhs_stride_c, par_off_c);
   return cudaGetLastError();
 }
