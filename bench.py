@@ -67,7 +67,10 @@ def parse():
     ap.add_argument("--prec", default="f32", choices=["f64", "df64", "f32", "f16", "bf16"], help="precision of --case mhat")
     ap.add_argument("--tensor-cores", type=int, default=0, help="--case mhat: 16-bit multi-RHS kernel on tensor cores")
     ap.add_argument("--shared-links", type=int, default=1,
-                    help="--case mhat: multi-RHS kernel with links and clover staged in shared memory")
+                    help="--case mhat: multi-RHS kernel with links and clover staged in shared memory (tile)")
+    ap.add_argument("--staged-spinors", type=int, default=0,
+                    help="--case mhat: multi-RHS kernel with cp.async-staged neighbour spinors (tuner off)")
+    ap.add_argument("--autotune", type=int, default=1, help="--case mhat: dslash autotuner on/off")
     return ap.parse_args()
 
 
@@ -377,6 +380,8 @@ def run_mhat_case(args):
     ctx = pkg.Context(dims)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_TENSOR_CORES, args.tensor_cores)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_SHARED_LINKS, args.shared_links)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_STAGED_SPINORS, args.staged_spinors)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_AUTOTUNE, args.autotune)
     ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, SEED)).cuda(), KAPPA, CSW)
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     psi = torch.from_numpy(W.gaussian_fermion(dims, 1, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(-1)
@@ -393,6 +398,7 @@ def run_mhat_case(args):
     gbs = st["dslash_bytes"] / (st["dslash_ms"] * 1e-3) / 1e9
     print(json.dumps({"case": "mhat", "lattice": dims, "nrhs": args.nrhs, "prec": args.prec,
                       "tensor_cores": args.tensor_cores, "shared_links": args.shared_links,
+                      "staged_spinors": args.staged_spinors, "autotune": args.autotune,
                       "dslash_launches": st["dslash_timed"], "avg_launch_ms": st["dslash_ms"] / st["dslash_timed"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind}))
     ctx.close()

@@ -239,6 +239,11 @@ typedef enum {
                                   channel and spin mixing on the tensor cores (mma.sync, BF16
                                   weights, inputs split into three BF16 terms, FP32 accumulation);
                                   0: FP32 SIMT mixing */
+  ,
+  WCL_OPT_STAGED_SPINORS = 5 /* 1: when the tuner is off, the multi-RHS dslash (16-site tiles)
+                                also stages each thread's neighbour spinors in shared memory with
+                                asynchronous copies (cp.async, two hops in flight); 0 (default):
+                                direct loads.  With the tuner on, both are candidates. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

@@ -446,6 +446,7 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
       break;
     case WCL_OPT_AUTOTUNE: c->autotune = value != 0; return WCL_OK;
     case WCL_OPT_PTC_TENSOR_CORES: c->ptc_tensor_cores = value != 0; return WCL_OK;
+    case WCL_OPT_STAGED_SPINORS: c->staged_spinors = value != 0; return WCL_OK;
   }
   set_error("wcl_set_option: unknown option %d or value %d", option, value);
   return WCL_ERR_INVALID_ARG;

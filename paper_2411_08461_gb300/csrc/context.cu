@@ -151,11 +151,12 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
+  const bool async = ch.variant == V_SMEM_ASYNC;
   switch (prec) {
-    case F64: return launch_dslash_mrhs<F64>(a, dagger, mode, ts, st);
-    case F32: return launch_dslash_mrhs<F32>(a, dagger, mode, ts, st);
-    case F16: return launch_dslash_mrhs<F16>(a, dagger, mode, ts, st);
-    default: return launch_dslash_mrhs<BF16>(a, dagger, mode, ts, st);
+    case F64: return launch_dslash_mrhs<F64>(a, dagger, mode, ts, st, async);
+    case F32: return launch_dslash_mrhs<F32>(a, dagger, mode, ts, st, async);
+    case F16: return launch_dslash_mrhs<F16>(a, dagger, mode, ts, st, async);
+    default: return launch_dslash_mrhs<BF16>(a, dagger, mode, ts, st, async);
   }
 }
 
@@ -176,10 +177,13 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   TuneChoice dflt{V_THREAD, c0->dslash_block[prec == DF64 ? F64 : prec]};
   if (tc_ok)
     dflt = {V_TC, tc_tile_sites()};
+  else if (mr_ok && c0->staged_spinors && prec != F64)
+    dflt = {V_SMEM_ASYNC, 16};
   else if (mr_ok)
     dflt = {V_SMEM, prec == F64 ? 16 : c0->shared_links};
   std::string key = "dslash p" + std::to_string(prec) + " m" + std::to_string(mode) + " d" + std::to_string(dagger) +
-                    " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok);
+                    " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok) +
+                    std::to_string((int)c0->staged_spinors);
   for (auto* c : ctxs)
     key += " " + std::to_string(c->lat.dims[0]) + "x" + std::to_string(c->lat.dims[1]) + "x" +
            std::to_string(c->lat.dims[2]) + "x" + std::to_string(c->lat.dims[3]);
@@ -197,7 +201,10 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   if (mr_ok) {
     cand.push_back({V_SMEM, 8});
     cand.push_back({V_SMEM, 16});
-    if (prec != F64) cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
+    if (prec != F64) {
+      cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
+      cand.push_back({V_SMEM_ASYNC, 16});
+    }
   }
   if (tc_ok) cand.push_back({V_TC, tc_tile_sites()});
   const int plain_mode = mode & 31;  // without the fused reduction

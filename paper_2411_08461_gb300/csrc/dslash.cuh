@@ -517,6 +517,109 @@ __device__ __forceinline__ SiteNbr site_neighbours(const LatGeom& g, int p, long
   return n;
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous staging of neighbour spinors (cp.async, 16-byte copies global ->
+// shared memory that do not occupy registers while in flight).  A thread's slot of
+// a stage holds the CH chunks of one spinor at [chunk][thread] (16 bytes each) and,
+// for the 16-bit formats, its norm.
+template <int P>
+struct SpinorStage;
+template <>
+struct SpinorStage<F64> {
+  static constexpr int CH = 12;
+  static constexpr bool NORM = false;
+};
+template <>
+struct SpinorStage<F32> {
+  static constexpr int CH = 6;
+  static constexpr bool NORM = false;
+};
+template <int P>
+struct SpinorStage16 {
+  static constexpr int CH = 3;
+  static constexpr bool NORM = true;
+};
+template <>
+struct SpinorStage<F16> : SpinorStage16<F16> {};
+template <>
+struct SpinorStage<BF16> : SpinorStage16<BF16> {};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// the "memory" clobbers keep the compiler from moving shared-memory reads of a
+// slot past the copies that refill it, or before the wait that completes it
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// issue the copies of the spinor at site j into stage slot (chunk stride nt uint4)
+template <int P>
+__device__ __forceinline__ void stage_issue(uint4* slot, float* nslot, int nt, const void* base, const float* norm,
+                                            long stride, long j) {
+  const uint4* g = static_cast<const uint4*>(base);
+#pragma unroll
+  for (int k = 0; k < SpinorStage<P>::CH; k++) cp_async16(slot + k * nt, g + k * stride + j);
+  if (SpinorStage<P>::NORM) cp_async4(nslot, norm + j);
+}
+
+template <int P>
+__device__ __forceinline__ void stage_read(cpx<float> v[12], const uint4* slot, const float* nslot, int nt);
+__device__ __forceinline__ void stage_read_f64(cpx<double> v[12], const uint4* slot, int nt) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const double2 d = reinterpret_cast<const double2*>(slot)[k * nt];
+    v[k] = {d.x, d.y};
+  }
+}
+template <>
+__device__ __forceinline__ void stage_read<F32>(cpx<float> v[12], const uint4* slot, const float*, int nt) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const float4 f = reinterpret_cast<const float4*>(slot)[k * nt];
+    v[2 * k] = {f.x, f.y};
+    v[2 * k + 1] = {f.z, f.w};
+  }
+}
+template <int P>
+__device__ __forceinline__ void stage_read16(cpx<float> v[12], const uint4* slot, const float* nslot, int nt) {
+  const float n = *nslot;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const uint4 q = slot[k * nt];
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      const float2 f = unpack2<P>(w[m]);
+      v[4 * k + m] = {f.x * n, f.y * n};
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void stage_read<F16>(cpx<float> v[12], const uint4* slot, const float* nslot, int nt) {
+  stage_read16<F16>(v, slot, nslot, nt);
+}
+template <>
+__device__ __forceinline__ void stage_read<BF16>(cpx<float> v[12], const uint4* slot, const float* nslot, int nt) {
+  stage_read16<BF16>(v, slot, nslot, nt);
+}
+
+// one hop (direction h = 2 mu + backward) from an already loaded neighbour spinor
+template <int MU, bool BACK, bool DAG, typename R>
+__device__ __forceinline__ void hop_from(cpx<R> acc[12], const cpx<R> psi[12], const R* U, R sign) {
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr int S = BACK ? -SF : SF;
+  cpx<R> h[6], uh[6];
+  project<MU, S>(psi, h);
+  link_mul_row<BACK>(U, h, uh, sign);
+  reconstruct_acc<MU, S>(acc, uh);
+}
+
 // Register cap: 8- and 16-site tiles keep 64 registers per thread (five 192-thread
 // or ten 96-thread CTAs per SM for 12 RHS); 32-site tiles (up to 512 threads) are
 // capped at 128.
@@ -535,8 +638,12 @@ struct MrhsBounds<32> {
   static constexpr int THREADS = 512, MIN_BLOCKS = 1;
 };
 
-template <int P, bool DAG, int MODE, int EPI, int TS>
-__global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsBounds<TS>::MIN_BLOCKS))
+// ASYNC: the eight neighbour spinors of a thread are staged through shared memory
+// with cp.async, two hops in flight (dynamic shared memory: 2 stages x CH chunks x
+// blockDim 16-byte slots, plus norms)
+template <int P, bool DAG, int MODE, int EPI, int TS, bool ASYNC = false>
+__global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
+                                  (P == F64 ? 1 : ASYNC ? MrhsBounds<TS>::MIN_BLOCKS - 1 : MrhsBounds<TS>::MIN_BLOCKS))
     dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
   using R = typename Traits<P>::R;
   constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
@@ -618,13 +725,54 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS, (P == F64 ? 1 : MrhsB
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
-    hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us[0][ls], Us[1][ls], R(1), R(1));
-    hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us[2][ls], Us[3][ls], R(1), R(1));
-    hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us[4][ls], Us[5][ls], R(1), R(1));
     const int tb = Tb[ls];
     const R sf = (tb & 1) ? R(g.tb) : R(1);
     const R sb = (tb & 2) ? R(g.tb) : R(1);
-    hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us[6][ls], Us[7][ls], sf, sb);
+    if constexpr (ASYNC) {
+      extern __shared__ uint4 stage_mem[];
+      const int nt = blockDim.x;
+      constexpr int CH = SpinorStage<P>::CH;
+      uint4* slot[2] = {stage_mem + threadIdx.x, stage_mem + CH * nt + threadIdx.x};
+      float* nslot[2] = {reinterpret_cast<float*>(stage_mem + 2 * CH * nt) + threadIdx.x,
+                         reinterpret_cast<float*>(stage_mem + 2 * CH * nt) + nt + threadIdx.x};
+      stage_issue<P>(slot[0], nslot[0], nt, in, in_norm, stride, Nb[0][ls]);
+      cp_async_commit();
+      stage_issue<P>(slot[1], nslot[1], nt, in, in_norm, stride, Nb[1][ls]);
+      cp_async_commit();
+#pragma unroll
+      for (int hh = 0; hh < 8; hh++) {
+        if (hh < 7)
+          cp_async_wait<1>();
+        else
+          cp_async_wait<0>();
+        cpx<R> psi[12];
+        if constexpr (P == F64)
+          stage_read_f64(psi, slot[hh & 1], nt);
+        else
+          stage_read<P>(psi, slot[hh & 1], nslot[hh & 1], nt);
+        const R sign = hh == 6 ? sf : hh == 7 ? sb : R(1);
+        switch (hh) {
+          case 0: hop_from<0, false, DAG>(acc, psi, Us[0][ls], sign); break;
+          case 1: hop_from<0, true, DAG>(acc, psi, Us[1][ls], sign); break;
+          case 2: hop_from<1, false, DAG>(acc, psi, Us[2][ls], sign); break;
+          case 3: hop_from<1, true, DAG>(acc, psi, Us[3][ls], sign); break;
+          case 4: hop_from<2, false, DAG>(acc, psi, Us[4][ls], sign); break;
+          case 5: hop_from<2, true, DAG>(acc, psi, Us[5][ls], sign); break;
+          case 6: hop_from<3, false, DAG>(acc, psi, Us[6][ls], sign); break;
+          default: hop_from<3, true, DAG>(acc, psi, Us[7][ls], sign); break;
+        }
+        // the slot's values are consumed: refill it with hop hh + 2
+        if (hh + 2 < 8) {
+          stage_issue<P>(slot[hh & 1], nslot[hh & 1], nt, in, in_norm, stride, Nb[hh + 2][ls]);
+          cp_async_commit();
+        }
+      }
+    } else {
+      hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us[0][ls], Us[1][ls], R(1), R(1));
+      hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us[2][ls], Us[3][ls], R(1), R(1));
+      hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us[4][ls], Us[5][ls], R(1), R(1));
+      hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us[6][ls], Us[7][ls], sf, sb);
+    }
     const R alpha = R(a.alpha[s.l]);
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
@@ -722,11 +870,28 @@ inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_
 }
 
 template <int P>
-cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st);
+cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st,
+                               bool async = false);
+
+// dynamic shared memory of the staged variant for `threads` threads
+template <int P>
+inline size_t mrhs_stage_bytes(int threads) {
+  return (size_t)2 * SpinorStage<P>::CH * threads * 16 + (SpinorStage<P>::NORM ? (size_t)2 * threads * 4 : 0);
+}
+
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 #define WCL_MRHS_CASE(P, DAG, MODE, EPI)                                                         \
   case (MODE) | ((DAG) ? 16 : 0) | ((EPI) << 5):                                                \
-    if (ts == 32)                                                                               \
+    if (async) {                                                                                \
+      const size_t sm = mrhs_stage_bytes<P>(threads);                                           \
+      cudaError_t ea = allow_dynamic_smem(dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, true>, sm); \
+      if (ea != cudaSuccess) return ea;                                                         \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, true><<<a.b.total_blocks, threads, sm, st>>>(a); \
+    } else if (ts == 32)                                                                        \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 32><<<a.b.total_blocks, threads, 0, st>>>(a);       \
     else if (ts == 8)                                                                           \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 8><<<a.b.total_blocks, threads, 0, st>>>(a);        \
@@ -738,7 +903,8 @@ cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int t
 // ts: sites per CTA (8, 16 or 32); the geometry a.b must have been built with that tile
 #define WCL_DEFINE_MRHS_LAUNCHER(P)                                                              \
   template <>                                                                                    \
-  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st) { \
+  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st, bool async) { \
+    if (async && ts != 16) return cudaErrorInvalidValue;                                         \
     const int threads = (ts * a.nrhs_tc + 31) / 32 * 32;                                         \
     int fin = 0;                                                                                 \
     switch (mode | (dagger ? 16 : 0)) {                                                          \

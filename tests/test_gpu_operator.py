@@ -192,5 +192,25 @@ def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
     lines = [l.split() for l in cache.read_text().splitlines() if "6x6x4x10" in l]
     assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
     for v, b, ms, *_ in lines:
-        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32)}
+        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32), (3, 16)}
         assert float(ms) > 0
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((8, 4, 4, 6), 7)])
+def test_apply_Mpc_multi_rhs_staged_spinors(pkg, dims, nrhs, dagger, prec):
+    """Multi-RHS kernel whose neighbour spinors arrive through shared memory by cp.async."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_STAGED_SPINORS
+
+    ctx, op, _ = _setup(pkg, dims, seed=23)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_STAGED_SPINORS, 1)
+    psi = W.gaussian_fermion(dims, 24, nrhs=nrhs)[:, 0].copy()
+    psi[1] *= 1e-7
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs, dagger=dagger)
+    got = host(out)
+    for k in range(nrhs):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL[prec], k
+    ctx.close()

@@ -100,11 +100,14 @@ def test_batch_of_uneven_lattices(pkg):
         c.close()
 
 
-@pytest.mark.parametrize("shared_links", [8, 16, 32, 0])
+@pytest.mark.parametrize("shared_links", [8, 16, 32, 0, "staged"])
 @pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
 def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
     """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials)."""
-    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS, WCL_OPT_STAGED_SPINORS
+
+    staged = shared_links == "staged"
+    shared_links = 16 if staged else shared_links
 
     shapes = [(4, 4, 4, 8), (6, 6, 2, 10)]
     ctxs, ops, bs, xs = [], [], [], []
@@ -113,6 +116,7 @@ def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
         c = pkg.Context(dims)
         c.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
         c.wcl_set_option(WCL_OPT_SHARED_LINKS, shared_links)
+        c.wcl_set_option(WCL_OPT_STAGED_SPINORS, int(staged))
         c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
         ctxs.append(c)
         ops.append(dirac.from_qdp_problem(g, dims, 0.1235, 1.0))
