@@ -305,7 +305,7 @@ template <>
 struct CloverChunk<F64> {
   static constexpr int NCH = 36, PER = 2;
   __device__ static void load(double r[2], const void* base, const float*, long stride, long i, int k) {
-    const double2 v = ldg(static_cast<const double2*>(base) + k * stride + i);
+    const double2 v = ldcs(static_cast<const double2*>(base) + k * stride + i);
     r[0] = v.x;
     r[1] = v.y;
   }
@@ -314,7 +314,7 @@ template <>
 struct CloverChunk<F32> {
   static constexpr int NCH = 18, PER = 4;
   __device__ static void load(float r[4], const void* base, const float*, long stride, long i, int k) {
-    const float4 v = ldg(static_cast<const float4*>(base) + k * stride + i);
+    const float4 v = ldcs(static_cast<const float4*>(base) + k * stride + i);
     r[0] = v.x;
     r[1] = v.y;
     r[2] = v.z;
@@ -325,8 +325,8 @@ template <int P>
 struct CloverChunk16 {
   static constexpr int NCH = 9, PER = 8;
   __device__ static void load(float r[8], const void* base, const float* norm, long stride, long i, int k) {
-    const uint4 q = ldg(static_cast<const uint4*>(base) + k * stride + i);
-    const float n = __ldg(norm + i);
+    const uint4 q = ldcs(static_cast<const uint4*>(base) + k * stride + i);
+    const float n = ldcs(norm + i);
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -680,10 +680,11 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
     const long i = site0 + ls;
     cpx<R> u[3][3];
     if (i < g.vh) {
+      // each link is read once per launch: evict-first, leaving L2 to the gathered spinors
       if (d & 1)
-        LinkIO<P>::load(u, a.gauge[s.l][1 - p], stride, Nb[d][ls], mu);
+        LinkIO<P>::template load<true>(u, a.gauge[s.l][1 - p], stride, Nb[d][ls], mu);
       else
-        LinkIO<P>::load(u, a.gauge[s.l][p], stride, i, mu);
+        LinkIO<P>::template load<true>(u, a.gauge[s.l][p], stride, i, mu);
     } else {
 #pragma unroll
       for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {R(0), R(0)};
@@ -778,7 +779,7 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
     for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
     if (MODE & MODE_XPAY) {
       cpx<R> xv[12];
-      SpinorIO<P>::load(xv, rhs_ptr<P>(a.x, s.l, rhs, stride), rhs_norm(a.x, s.l, rhs, stride), stride, i);
+      SpinorIO<P>::load_cs(xv, rhs_ptr<P>(a.x, s.l, rhs, stride), rhs_norm(a.x, s.l, rhs, stride), stride, i);
       const R beta = R(a.beta[s.l]);
       if (MODE & MODE_PRE) {
         hermitian6_axpy_row(acc, beta, Cs[CLOV ? ls : 0], xv);
@@ -789,7 +790,7 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
       }
       if (EPI == EPI_ALPHA) {
         cpx<R> fv[12];
-        SpinorIO<P>::load(fv, rhs_ptr<P>(a.f, s.l, rhs, stride), rhs_norm(a.f, s.l, rhs, stride), stride, i);
+        SpinorIO<P>::load_cs(fv, rhs_ptr<P>(a.f, s.l, rhs, stride), rhs_norm(a.f, s.l, rhs, stride), stride, i);
         dot_acc(red, fv, acc);
       } else if (EPI == EPI_OMEGA) {
         dot_acc(red, acc, xv);
@@ -801,9 +802,11 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
     if (MODE & MODE_POST) {
       cpx<R> y2[12];
       clover_apply_smem<R>(y2, acc, Cs[CLOV ? ls : 0]);
-      SpinorIO<P>::store(y2, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
+      SpinorIO<P>::template store<true>(y2, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride),
+                                        stride, i);
     } else {
-      SpinorIO<P>::store(acc, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride), stride, i);
+      SpinorIO<P>::template store<true>(acc, rhs_ptr_w<P>(a.out, s.l, rhs, stride), rhs_norm(a.out, s.l, rhs, stride),
+                                        stride, i);
     }
   }
   if constexpr (EPI != EPI_NONE) {

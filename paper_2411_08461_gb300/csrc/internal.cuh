@@ -240,6 +240,24 @@ __device__ __forceinline__ float4 ldg(const float4* p) { return __ldg(p); }
 __device__ __forceinline__ uint4 ldg(const uint4* p) { return __ldg(p); }
 __device__ __forceinline__ uint2 ldg(const uint2* p) { return __ldg(p); }
 __device__ __forceinline__ float ldg(const float* p) { return __ldg(p); }
+// evict-first ("streaming") loads and stores, for data a launch touches once
+__device__ __forceinline__ double2 ldcs(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ldcs(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ uint4 ldcs(const uint4* p) { return __ldcs(p); }
+__device__ __forceinline__ uint2 ldcs(const uint2* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldcs(const float* p) { return __ldcs(p); }
+template <bool CS, typename T>
+__device__ __forceinline__ T ldp(const T* p) {
+  if (CS) return ldcs(p);
+  return ldg(p);
+}
+template <bool CS, typename T>
+__device__ __forceinline__ void stp(T* p, const T& v) {
+  if (CS)
+    __stcs(p, v);
+  else
+    *p = v;
+}
 // NC = true: non-coherent read-only path (field not written by this kernel);
 // NC = false: ordinary load (field updated in place by the same kernel).
 template <bool NC, typename T>
@@ -265,10 +283,19 @@ struct SpinorIO<F64> {
       v[k] = {d.x, d.y};
     }
   }
+  template <bool CS = false>
   __device__ static void store(const cpx<R> v[12], void* base, float*, long stride, long i) {
     double2* p = static_cast<double2*>(base);
 #pragma unroll
-    for (int k = 0; k < 12; k++) p[k * stride + i] = make_double2(v[k].re, v[k].im);
+    for (int k = 0; k < 12; k++) stp<CS>(p + k * stride + i, make_double2(v[k].re, v[k].im));
+  }
+  __device__ static void load_cs(cpx<R> v[12], const void* base, const float*, long stride, long i) {
+    const double2* p = static_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double2 d = ldcs(p + k * stride + i);
+      v[k] = {d.x, d.y};
+    }
   }
 };
 
@@ -304,10 +331,21 @@ struct SpinorIO<F32> {
       v[2 * k + 1] = {f.z, f.w};
     }
   }
+  template <bool CS = false>
   __device__ static void store(const cpx<R> v[12], void* base, float*, long stride, long i) {
     float4* p = static_cast<float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 6; k++) p[k * stride + i] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    for (int k = 0; k < 6; k++)
+      stp<CS>(p + k * stride + i, make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im));
+  }
+  __device__ static void load_cs(cpx<R> v[12], const void* base, const float*, long stride, long i) {
+    const float4* p = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float4 f = ldcs(p + k * stride + i);
+      v[2 * k] = {f.x, f.y};
+      v[2 * k + 1] = {f.z, f.w};
+    }
   }
 };
 
@@ -328,13 +366,14 @@ struct SpinorIO16 {
       v[4 * k + 3] = {d.x * n, d.y * n};
     }
   }
+  template <bool CS = false>
   __device__ static void store(const cpx<R> v[12], void* base, float* norm, long stride, long i) {
     uint4* p = static_cast<uint4*>(base);
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
     float inv = m > 0.f ? 1.0f / m : 0.f;
-    norm[i] = m;
+    stp<CS>(norm + i, m);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
       uint4 q;
@@ -342,7 +381,21 @@ struct SpinorIO16 {
       q.y = pack2<P>(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
       q.z = pack2<P>(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
       q.w = pack2<P>(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
-      p[k * stride + i] = q;
+      stp<CS>(p + k * stride + i, q);
+    }
+  }
+  __device__ static void load_cs(cpx<R> v[12], const void* base, const float* norm, long stride, long i) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float n = ldcs(norm + i);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint4 q = ldcs(p + k * stride + i);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int m = 0; m < 4; m++) {
+        const float2 f = unpack2<P>(w[m]);
+        v[4 * k + m] = {f.x * n, f.y * n};
+      }
     }
   }
 };
@@ -367,11 +420,12 @@ __device__ __forceinline__ void reconstruct_row2(cpx<R> u[3][3]) {
 template <>
 struct LinkIO<F64> {
   using R = double;
+  template <bool CS = false>
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
     const double2* p = static_cast<const double2*>(base) + (long)mu * 9 * stride;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      double2 d = ldg(p + k * stride + i);
+      double2 d = ldp<CS>(p + k * stride + i);
       u[k / 3][k % 3] = {d.x, d.y};
     }
   }
@@ -391,9 +445,10 @@ struct LinkIO<DF64> {
 template <>
 struct LinkIO<F32> {
   using R = float;
+  template <bool CS = false>
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
     const float4* p = static_cast<const float4*>(base) + (long)mu * 3 * stride;
-    float4 a = ldg(p + i), b = ldg(p + stride + i), c = ldg(p + 2 * stride + i);
+    float4 a = ldp<CS>(p + i), b = ldp<CS>(p + stride + i), c = ldp<CS>(p + 2 * stride + i);
     u[0][0] = {a.x, a.y};
     u[0][1] = {a.z, a.w};
     u[0][2] = {b.x, b.y};
@@ -406,9 +461,10 @@ struct LinkIO<F32> {
 template <int P>
 struct LinkIO16 {
   using R = float;
+  template <bool CS = false>
   __device__ static void load(cpx<R> u[3][3], const void* base, long stride, long i, int mu) {
     const uint2* p = static_cast<const uint2*>(base) + (long)mu * 3 * stride;
-    uint2 a = ldg(p + i), b = ldg(p + stride + i), c = ldg(p + 2 * stride + i);
+    uint2 a = ldp<CS>(p + i), b = ldp<CS>(p + stride + i), c = ldp<CS>(p + 2 * stride + i);
     float2 t;
     t = unpack2<P>(a.x); u[0][0] = {t.x, t.y};
     t = unpack2<P>(a.y); u[0][1] = {t.x, t.y};
