@@ -244,6 +244,12 @@ typedef enum {
                                 also stages each thread's neighbour spinors in shared memory with
                                 asynchronous copies (cp.async, two hops in flight); 0 (default):
                                 direct loads.  With the tuner on, both are candidates. */
+  ,
+  WCL_OPT_BLOCKED_TILES = 6 /* 1: when the tuner is off, the multi-RHS dslash walks its tiles in
+                               blocks of z planes on lattices with more than 512 tiles per time
+                               slice, so that the t neighbours of a site are still in L2 (DRAM
+                               traffic 1.07x instead of 1.25x the algorithmic bytes at 32^3x64);
+                               0 (default): site order.  With the tuner on, both are candidates. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

@@ -131,6 +131,19 @@ int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
   return (int)m;
 }
 
+// z planes per block of the multi-RHS kernel's tile order: the largest divisor of
+// Lz keeping Ly * zblk * (tiles per row) <= 512 tiles between a site and its t
+// neighbours; 0 (site order) when tiles are not whole parts of x rows or the lattice
+// is small enough for site order to keep them in L2 anyway
+static int mrhs_zblock(const LatGeom& g, int ts) {
+  if (g.lxh % ts != 0) return 0;
+  const long tpr = g.lxh / ts, Ly = g.dims[1], Lz = g.dims[2];
+  if (Ly * Lz * tpr <= 512) return 0;
+  for (int bz = Lz; bz >= 1; bz--)
+    if (Lz % bz == 0 && Ly * bz * tpr <= 512) return bz;
+  return 1;
+}
+
 // ---------------------------------------------------------------------------
 // Kernel variants of one dslash configuration and their launch.
 static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, int nrhs, DslashArgs a, bool dagger,
@@ -148,7 +161,10 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   // one CTA covers all right-hand sides of its sites
   const int ts = ch.variant == V_TC ? tc_tile_sites() : ch.block;
   a.b = make_batch(ctxs, 1, ts, 0);
-  for (size_t l = 0; l < ctxs.size(); l++) a.b.lat[l].slot_base = (int)l * nrhs;
+  for (size_t l = 0; l < ctxs.size(); l++) {
+    a.b.lat[l].slot_base = (int)l * nrhs;
+    if (ch.variant == V_SMEM_ZB) a.b.lat[l].zblk = mrhs_zblock(a.b.lat[l], ts);
+  }
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
   const bool async = ch.variant == V_SMEM_ASYNC;
@@ -179,11 +195,13 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
     dflt = {V_TC, tc_tile_sites()};
   else if (mr_ok && c0->staged_spinors && prec != F64)
     dflt = {V_SMEM_ASYNC, 16};
+  else if (mr_ok && c0->blocked_tiles)
+    dflt = {V_SMEM_ZB, 16};
   else if (mr_ok)
     dflt = {V_SMEM, prec == F64 ? 16 : c0->shared_links};
   std::string key = "dslash p" + std::to_string(prec) + " m" + std::to_string(mode) + " d" + std::to_string(dagger) +
                     " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok) +
-                    std::to_string((int)c0->staged_spinors);
+                    std::to_string((int)c0->staged_spinors) + std::to_string((int)c0->blocked_tiles);
   for (auto* c : ctxs)
     key += " " + std::to_string(c->lat.dims[0]) + "x" + std::to_string(c->lat.dims[1]) + "x" +
            std::to_string(c->lat.dims[2]) + "x" + std::to_string(c->lat.dims[3]);
@@ -205,6 +223,15 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
       cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
       cand.push_back({V_SMEM_ASYNC, 16});
     }
+    bool zb = false;
+    for (auto* c : ctxs) {
+      LatGeom gg{};
+      gg.lxh = c->lat.dims[0] / 2;
+      gg.dims[1] = c->lat.dims[1];
+      gg.dims[2] = c->lat.dims[2];
+      zb = zb || mrhs_zblock(gg, 16) > 0;
+    }
+    if (zb) cand.push_back({V_SMEM_ZB, 16});
   }
   if (tc_ok) cand.push_back({V_TC, tc_tile_sites()});
   const int plain_mode = mode & 31;  // without the fused reduction

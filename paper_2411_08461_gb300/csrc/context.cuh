@@ -61,6 +61,7 @@ struct wcl_ctx {
   bool autotune = true;       // time the dslash variants of a new configuration on first use
   bool ptc_tensor_cores = true;  // BF16 network layers mix channels on the tensor cores
   bool staged_spinors = false;   // untuned multi-RHS dslash: cp.async-staged neighbour spinors
+  bool blocked_tiles = false;    // untuned multi-RHS dslash: tiles in z blocks (large lattices)
   int blas_block = 256;
 };
 
@@ -154,7 +155,9 @@ bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
 // Autotuner: the dslash variant of a configuration (precision, mode, RHS count,
 // lattice shapes, options) is picked by timing the candidates on first use and
 // kept for the process; with WCL_TUNE_CACHE=<file> choices persist across runs.
-enum TuneVariant { V_THREAD = 0, V_SMEM = 1, V_TC = 2, V_SMEM_ASYNC = 3 };
+// V_SMEM_ZB: the shared-memory kernel walking its tiles in z blocks (L2 reuse of the
+// t neighbours on large lattices)
+enum TuneVariant { V_THREAD = 0, V_SMEM = 1, V_TC = 2, V_SMEM_ASYNC = 3, V_SMEM_ZB = 4 };
 struct TuneChoice {
   int variant;  // TuneVariant
   int block;    // threads per CTA (V_THREAD) or sites per CTA (V_SMEM, V_SMEM_ASYNC, V_TC)

@@ -658,7 +658,24 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
   const int slot0 = s.l * nrhs;
   const int p = a.out_parity;
   const long stride = g.stride;
-  const long site0 = (long)s.chunk * TS;
+  long tile = s.chunk;
+  if (g.zblk > 0) {
+    // blocked order (z blocks outermost, then t, z in the block, y, x tile): the t
+    // neighbours of a site are gathered Ly * zblk tiles apart instead of Ly * Lz, so
+    // they are still in L2 (tiles are whole x rows or exact parts of one)
+    const int tpr = g.lxh / TS, Ly = g.dims[1], Lz = g.dims[2], Lt = g.dims[3], bz = g.zblk;
+    long q = tile;
+    const int xt = (int)(q % tpr);
+    q /= tpr;
+    const int y = (int)(q % Ly);
+    q /= Ly;
+    const int zz = (int)(q % bz);
+    q /= bz;
+    const int t = (int)(q % Lt);
+    const int zb = (int)(q / Lt);
+    tile = (((long)t * Lz + zb * bz + zz) * Ly + y) * tpr + xt;
+  }
+  const long site0 = tile * TS;
 
   // phase 0: coordinates and neighbours of the tile's sites, once for all RHS
   if (threadIdx.x < TS) {

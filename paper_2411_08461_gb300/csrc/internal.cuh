@@ -623,6 +623,7 @@ struct LatGeom {
   int nchunk;       // site blocks per RHS
   int slot_base;    // index of (lattice, rhs = 0) in per-slice arrays
   float tb;         // fermion time boundary sign
+  int zblk;         // multi-RHS kernel: z planes per block of its tile order (0: tiles in site order)
 };
 
 struct Batch {

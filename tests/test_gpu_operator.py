@@ -192,7 +192,8 @@ def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
     lines = [l.split() for l in cache.read_text().splitlines() if "6x6x4x10" in l]
     assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
     for v, b, ms, *_ in lines:
-        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32), (3, 16)}
+        assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32), (3, 16),
+                                    (4, 16)}
         assert float(ms) > 0
 
 
@@ -213,4 +214,23 @@ def test_apply_Mpc_multi_rhs_staged_spinors(pkg, dims, nrhs, dagger, prec):
     got = host(out)
     for k in range(nrhs):
         assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL[prec], k
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "f64"])
+def test_multi_rhs_blocked_tile_order(pkg, prec):
+    """32x24x24x4: Ly * Lz > 512 tiles per time slice, so with blocked tiles the
+    multi-RHS kernel walks its 16-site tiles in blocks of 12 z planes."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_BLOCKED_TILES
+
+    dims = (32, 24, 24, 4)
+    ctx, op, _ = _setup(pkg, dims, seed=25)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_BLOCKED_TILES, 1)
+    psi = W.gaussian_fermion(dims, 26, nrhs=5)[:, 0].copy()
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=5)
+    got = host(out)
+    for k in range(5):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], False)) <= TOL[prec], k
     ctx.close()
