@@ -41,6 +41,7 @@ EPS, SEED, KAPPA, CSW, TOL = 0.3, 0, 0.1235, 1.0, 1e-10
 METRIC = "clover dslash GB/s & roofline %; 12-RHS solve time to 1e-10 true residual"
 PREC_INDEX = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 vector rate, nominal
+TRAFFIC_F32_32C64_12RHS = (2 * 3.86e9 + 5.90e9 + 4.64e9) / 4  # measured DRAM bytes per launch (see run_ours)
 UNIT = "12-RHS solves/s"
 WORKLOAD = "32^3x64 Wilson-clover, eps 0.3, kappa 0.1235, c_sw 1.0, 12 spin-colour point sources, tol 1e-10"
 
@@ -323,7 +324,11 @@ def run_ours(args, rank, world, local):
     df_ms, df_n = st["prec_ms"][4], st["prec_timed"][4]
     f64_gflops = f64["dslash_flops"] / (f64["dslash_ms"] * 1e-3) / 1e9 if f64["dslash_ms"] > 0 else None
     f32_gbs = f32["dslash_bytes"] / (f32["dslash_ms"] * 1e-3) / 1e9 if f32["dslash_ms"] > 0 else None
-    traffic = os.environ.get("WCL_DSLASH_TRAFFIC")
+    # DRAM bytes (read + written) per inner-dslash launch of this solve, averaged over
+    # its launch mix (2 x A^-1 D, 1 x alpha-fused, 1 x omega-fused per iteration), from
+    # an ncu capture of the same launches at 32^3x64, 12 RHS, FP32 (1 pass,
+    # dram__bytes_read.sum + dram__bytes_write.sum): 3.86, 5.90 and 4.64 GB
+    traffic = TRAFFIC_F32_32C64_12RHS if (dims == DIMS and args.sloppy == "f32") else None
     value = world * 1e3 / ms
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -340,7 +345,7 @@ def run_ours(args, rank, world, local):
                      "frac": (gbs / peak) if gbs else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": s_bytes / max(1, s_n), "launches_timed": s_n,
                      "avg_launch_ms": s_ms / max(1, s_n),
-                     "traffic": float(traffic) if traffic else None,
+                     "traffic": traffic,
                      "gflops": s_flops / (s_ms * 1e-3) / 1e9 if s_ms > 0 else None,
                      "share_of_profiled_solve": s_ms / max(1e-9, pinfos[0]["seconds"] * 1e3)},
         "fp64_dslash": {"bound": "alu", "kernel": "FP64 12-RHS fused dslash (final residual replacements)",
