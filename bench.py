@@ -102,9 +102,21 @@ def max_over_ranks(x, world):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replicas_value(max_ms, world):
+    """Whole-job solves per second: every rank finished one solve per step, timed by
+    the slowest rank."""
+    return world * 1e3 / max_ms
+
+
+def replica_seed(rank):
+    """Replicas only: every rank solves its own gauge field, seeded by its rank."""
+    return SEED + rank
 
 
 class Clocks:
@@ -234,7 +246,7 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    seed = SEED + rank  # replicas: every rank solves its own gauge field
+    seed = replica_seed(rank)
     dims = tuple(int(v) for v in args.dims.split(","))
     gauge = W.gauge_links(dims, EPS, seed)
     src = np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])
@@ -330,7 +342,7 @@ def run_ours(args, rank, world, local):
     # an ncu capture of the same launches at 32^3x64, 12 RHS, FP32 (1 pass,
     # dram__bytes_read.sum + dram__bytes_write.sum): 3.86, 5.90 and 4.64 GB
     traffic = TRAFFIC_F32_32C64_12RHS if (dims == DIMS and args.sloppy == "f32") else None
-    value = world * 1e3 / ms
+    value = replicas_value(ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
