@@ -848,19 +848,33 @@ struct TcChunks {
 };
 
 template <int EPI>
-__global__ void __launch_bounds__(256) tc_epi_finalize_kernel(const double* __restrict__ partials, int maxch,
-                                                              TcChunks ch, const int* __restrict__ active,
-                                                              Scalars* sc) {
+__global__ void __launch_bounds__(1024) tc_epi_finalize_kernel(const double* __restrict__ partials, int maxch,
+                                                               TcChunks ch, const int* __restrict__ active,
+                                                               Scalars* sc) {
   const int slot = blockIdx.x;
   if (active && !active[slot]) return;
   const int n = ch.nch[slot / ch.nrhs];
-  double acc[3] = {0, 0, 0};
-  for (int c = threadIdx.x; c < n; c += blockDim.x)
-    for (int k = 0; k < 3; k++) acc[k] += partials[((size_t)slot * maxch + c) * 3 + k];
-  __shared__ double sh[3][8];
+  const double* part = partials + (size_t)slot * maxch * 3;
+  // four independent partial sums per thread keep four loads in flight (fixed order:
+  // the result does not depend on timing)
+  double acc[4][3] = {};
+  for (int c0 = threadIdx.x; c0 < n; c0 += 4 * blockDim.x) {
+    double v[4][3];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int c = c0 + u * blockDim.x;
+#pragma unroll
+      for (int k = 0; k < 3; k++) v[u][k] = c < n ? part[(size_t)c * 3 + k] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) acc[u][k] += v[u][k];
+  }
+  __shared__ double sh[3][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < 3; k++) {
-    double v = warp_sum(acc[k]);
+    double v = warp_sum((acc[0][k] + acc[1][k]) + (acc[2][k] + acc[3][k]));
     if (lane == 0) sh[k][warp] = v;
   }
   __syncthreads();
@@ -880,10 +894,10 @@ inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_
   for (int l = 0; l < MAXLAT; l++) ch.nch[l] = l < a.b.nlat ? a.b.lat[l].nchunk : 0;
   const int nslot = a.b.nlat * a.nrhs_tc;
   switch (epi) {
-    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<nslot, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
     default: return cudaSuccess;
   }
   return cudaGetLastError();
