@@ -365,11 +365,6 @@ struct BicgUpdate {  // x += alpha p + omega s; r = s - omega t; then rho' and |
   __device__ void finalize(Scalars& c, const double* t) const { bicg_rho_finalize(c, make_double2(t[0], t[1]), t[2], RHO_NORMAL); }
 };
 
-// reliable update: r64 = b_e - y with y = A_ee x_e - kappa D_eo x_o already in
-// r64 (x_o the reconstructed odd solution), so r64 is the FP64 Schur residual
-// b_hat - M_hat x_e; rS = r64.  ro holds the odd residual b_o - (A_oo x_o - kappa D_oe x_e).
-// aux[0] = ||r_e||^2, aux[3] = ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true residual).
-// BiCGStab also recomputes rho against rhat (REPLACE).
 // One field of precision Q (F64 or DF64) read as FP64 values.
 template <int Q>
 __device__ __forceinline__ void load_as_f64(cpx<double> v[12], const void* base, long stride, long i);
@@ -385,9 +380,13 @@ __device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void*
   for (int k = 0; k < 12; k++) v[k] = {double(d[k].re), double(d[k].im)};
 }
 
-// r64 holds the operator result A_ee x_e - kappa D_eo x_o in precision Q and is
-// overwritten, in place, by the FP64 residual b_hat - (that); ro, when given,
-// holds the odd residual of the reconstruction (precision Q).
+// Reliable update: r64 holds y = A_ee x_e - kappa D_eo x_o in precision Q (x_o the
+// reconstructed odd solution) and is overwritten, in place, by the FP64 residual
+// r_e = b_e - y, which equals the Schur residual b_hat - M_hat x_e; rS = r_e in the
+// inner precision.  ro, when given, holds the odd residual b_o - (A_oo x_o - kappa
+// D_oe x_e) of the reconstruction (precision Q).  aux[0] = ||r_e||^2, aux[3] =
+// ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true residual); BiCGStab also
+// recomputes rho against rhat (REPLACE).
 template <int S, int Q>
 struct ResidualReplace {
   FieldRef r64, bhat, rS, rhat, ro;
