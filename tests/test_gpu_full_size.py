@@ -62,13 +62,15 @@ def test_schur_operator_12rhs_sampled(problem, prec):
         assert np.linalg.norm(g - ref) <= TOL[prec] * np.linalg.norm(ref), (prec, k)
 
 
-def test_twelve_source_solve_sampled_residual(problem):
-    """The bench's solve (FP32 inner solver, delta 3e-4, checks every 2 iterations):
-    every sampled site of b - M x is below 1e-10 ||b||, site 0 (the sources) included."""
+@pytest.mark.parametrize("sloppy,delta", [("f32", 3e-4), ("f16", 0.03), ("bf16", 0.1)])
+def test_twelve_source_solve_sampled_residual(problem, sloppy, delta):
+    """The bench's solve (FP32 inner solver, delta 3e-4, checks every 2 iterations) and
+    its 16-bit variants: every sampled site of b - M x is below 1e-10 ||b||, site 0 (the
+    sources) included; every RHS reports an FP64 true residual below 1e-10."""
     pkg, ctx, gauge = problem
     b = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
     x = cuda(np.zeros_like(b))
-    prm = pkg.wcl_default_params(solver="bicgstab", sloppy="f32", tol=1e-10, check_every=2, delta_reliable=3e-4)
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=sloppy, tol=1e-10, check_every=2, delta_reliable=delta)
     _, info = ctx.wcl_invert(x, cuda(b), 12, prm)
     xh = host(x)
     assert all(i["true_residual"] <= 1e-10 and i["status"] == 0 for i in info), info
