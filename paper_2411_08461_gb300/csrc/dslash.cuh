@@ -366,15 +366,6 @@ struct SmemRow<double> {
     o[1] = v.y;
   }
 };
-template <typename R, int N>
-__device__ __forceinline__ void smem_read(R out[N], const R* row) {
-  constexpr int PER = SmemRow<R>::PER;
-  R t[(N + PER - 1) / PER * PER];
-#pragma unroll
-  for (int k = 0; k < (N + PER - 1) / PER; k++) SmemRow<R>::get(t + PER * k, row, k);
-#pragma unroll
-  for (int k = 0; k < N; k++) out[k] = t[k];
-}
 
 // lower-triangle packing of a 6x6 block: entry k = r (r - 1) / 2 + c, c < r
 __host__ __device__ constexpr int tri_row(int k) { return k < 1 ? 1 : k < 3 ? 2 : k < 6 ? 3 : k < 10 ? 4 : 5; }
