@@ -35,7 +35,8 @@
  *
  * Ownership and execution:
  *   - every d_* pointer is caller-owned, contiguous device memory (e.g. a
- *     torch tensor's data_ptr()), and must stay valid for the duration of the
+ *     torch tensor's data_ptr()) -- fermion buffers may also be page-locked host
+ *     memory, see wcl_apply_D -- and must stay valid for the duration of the
  *     call; the library never frees it;
  *   - the library owns its internal copies (reordered links, clover, solver
  *     workspace) and frees them in wcl_destroy;
@@ -76,9 +77,10 @@ typedef enum {
   WCL_F32 = 1,
   WCL_F16 = 2,   /* FP16 storage with per-site norms, FP32 arithmetic */
   WCL_BF16 = 3,  /* BF16 storage with per-site norms, FP32 arithmetic */
-  WCL_DF64 = 4   /* FP64 fields, double-float arithmetic (two FP32, ~48-bit significand);
-                    wcl_apply_D / wcl_apply_Mpc only.  The solvers use it for residual
-                    replacements in the middle of a solve; every reported residual is FP64. */
+  WCL_DF64 = 4   /* double-float: every FP64 value stored as an FP32 pair (hi, lo), ~48-bit
+                    significand, arithmetic on the FP32 pipes; for wcl_apply_D /
+                    wcl_apply_Mpc, and as wcl_solve_params.outer for the residual
+                    replacements in the middle of a solve (every reported residual is FP64). */
 } wcl_prec;
 
 typedef enum {
@@ -142,8 +144,8 @@ wcl_status wcl_load_gauge(wcl_ctx* ctx, const void* d_gauge, double kappa, doubl
 /* Fermion buffers (d_in, d_out, d_x, d_b below) are device memory of the
  * context's GPU, or page-locked host memory (cudaHostAlloc / cudaHostRegister),
  * which the import and export kernels read and write in place through its device
- * alias over the host link; anything else gives WCL_ERR_INVALID_ARG.  Work is
- * ordered on the caller's stream: synchronise it before reading host outputs.
+ * alias over the host link; anything else gives WCL_ERR_INVALID_ARG.  As for
+ * device buffers, the results are complete when the call returns.
  *
  * d_out = M d_in on the whole lattice for nrhs fields (QDP layout, complex128),
  * computed in precision prec (links, clover and spinors stored in prec). */
