@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--delta", type=float, default=3e-4, help="reliable-update threshold")
     ap.add_argument("--check-every", type=int, default=2, help="iterations per graph replay / convergence check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pairs", type=int, default=512, help="training pairs of --case compare")
+    ap.add_argument("--pairs", type=int, default=2000, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
     ap.add_argument("--case", default="solve", choices=["solve", "mhat", "compare", "batch", "throughput", "precond"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures); "

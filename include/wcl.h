@@ -219,6 +219,15 @@ wcl_status wcl_precond_loss_grad(wcl_ctx* ctx, const void* d_r_e, const void* d_
 wcl_status wcl_precond_train(wcl_ctx* ctx, const void* d_r_e, const void* d_e_e, int npairs,
                              const wcl_train_params* params, double* h_loss_per_epoch);
 
+/* Propagator layout (Sec. II.A): [2][Lt][Lz][Ly][Lx/2][Ns][Ns][Nc][Nc] complex128
+ * with sink-source spin and sink-source colour order.  The twelve solutions of
+ * wcl_invert for the spin-colour sources k = 3 * spin + colour ([12][fermion]) are
+ * its source columns: prop[..., s, s0, c, c0] = x[3 s0 + c0][..., s, c].
+ *   d_prop, d_x12: device or page-locked host memory (as the fermion buffers of
+ *   wcl_apply_D), caller-owned, not overlapping.  Pure data movement (bit exact). */
+wcl_status wcl_fermions_to_propagator(wcl_ctx* ctx, void* d_prop, const void* d_x12);
+wcl_status wcl_propagator_to_fermions(wcl_ctx* ctx, void* d_x12, const void* d_prop);
+
 /* Options of a context (wcl_set_option). */
 typedef enum {
   WCL_OPT_TENSOR_CORES = 1 /* 1: 16-bit multi-RHS dslash (4..16 RHS) with the link and clover

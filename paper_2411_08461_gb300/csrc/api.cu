@@ -338,6 +338,26 @@ wcl_status wcl_apply_Mpc(wcl_ctx* c, void* d_out_e, const void* d_in_e, wcl_prec
   return s;
 }
 
+static wcl_status propagator_call(wcl_ctx* c, void* dst, const void* src, int to_prop, const char* name) {
+  if (!c || !dst || !src) {
+    set_error("%s: invalid argument", name);
+    return WCL_ERR_INVALID_ARG;
+  }
+  if (!field_ptr(c, dst, &dst, name) || !field_ptr(c, src, &src, name)) return WCL_ERR_INVALID_ARG;
+  WCL_CHECK(enter(c));
+  WCL_CUDA(propagator_layout(c->lat, src, dst, to_prop, c->stream));
+  count_launch(c);
+  return leave(c, WCL_OK);
+}
+
+wcl_status wcl_fermions_to_propagator(wcl_ctx* c, void* d_prop, const void* d_x12) {
+  return propagator_call(c, d_prop, d_x12, 1, "wcl_fermions_to_propagator");
+}
+
+wcl_status wcl_propagator_to_fermions(wcl_ctx* c, void* d_x12, const void* d_prop) {
+  return propagator_call(c, d_x12, d_prop, 0, "wcl_propagator_to_fermions");
+}
+
 static wcl_status check_params(const wcl_solve_params* p) {
   if (!p || (p->outer != WCL_F64 && p->outer != WCL_DF64) || !valid_prec(p->sloppy) || !(p->tol > 0) ||
       p->maxiter < 1 ||

@@ -352,6 +352,22 @@ __global__ void __launch_bounds__(128) fermion_export_kernel(const double2* __re
   }
 }
 
+// [12][site][Ns][Nc] (source k = 3 s0 + c0) <-> [site][Ns][Ns][Nc][Nc]: one thread per
+// (site, 16-byte complex) of the propagator; to_prop selects the direction
+__global__ void propagator_kernel(const double2* __restrict__ src, double2* __restrict__ dst, long nsite, int to_prop) {
+  const long n = nsite * 144;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const long site = e / 144;
+    const int q = (int)(e % 144);  // propagator index ((s * 4 + s0) * 3 + c) * 3 + c0
+    const int c0 = q % 3, c = (q / 3) % 3, s0 = (q / 9) % 4, s = q / 36;
+    const long f = ((long)(3 * s0 + c0) * nsite + site) * 12 + 3 * s + c;  // fermion index
+    if (to_prop)
+      dst[e] = src[f];
+    else
+      dst[f] = src[e];
+  }
+}
+
 // ---------------------------------------------------------------------------
 static int grid_for(long n, int block) {
   long g = (n + block - 1) / block;
@@ -442,4 +458,13 @@ cudaError_t export_fermion(const LatticeDevice& L, const void* d_src64, int nrhs
   return cudaGetLastError();
 }
 
+}  // namespace wcl
+
+namespace wcl {
+cudaError_t propagator_layout(const LatticeDevice& L, const void* src, void* dst, int to_prop, cudaStream_t st) {
+  const long nsite = 2 * L.vh;
+  propagator_kernel<<<grid_for(nsite * 144, 256), 256, 0, st>>>(static_cast<const double2*>(src),
+                                                                static_cast<double2*>(dst), nsite, to_prop);
+  return cudaGetLastError();
+}
 }  // namespace wcl

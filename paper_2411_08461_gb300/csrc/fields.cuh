@@ -45,6 +45,9 @@ inline size_t clover_parity_bytes(int prec, long stride) {
   }
 }
 
+// 12 fermion fields (sources k = 3 spin + colour) <-> one propagator field, QDP layouts
+cudaError_t propagator_layout(const LatticeDevice& L, const void* src, void* dst, int to_prop, cudaStream_t st);
+
 // d_flags bits: 1 non-finite input, 2 link not SU(3), 4 singular clover block
 cudaError_t import_gauge(const LatticeDevice& L, const void* d_qdp, int* d_flags, cudaStream_t st);
 cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw, int* d_flags,

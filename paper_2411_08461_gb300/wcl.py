@@ -77,6 +77,8 @@ SIGNATURES = {
     "wcl_load_gauge": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double]),
     "wcl_apply_D": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "wcl_apply_Mpc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "wcl_fermions_to_propagator": (ctypes.c_int, [_P, _P, _P]),
+    "wcl_propagator_to_fermions": (ctypes.c_int, [_P, _P, _P]),
     "wcl_invert": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_solve_params),
                                   ctypes.POINTER(wcl_solve_info)]),
     "wcl_invert_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -248,6 +250,23 @@ class Context:
         _check(load_library().wcl_precond_apply(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
                                                 _ptr(in_e, torch.complex128, n, "in_e"), nrhs, int(bf16)),
                "wcl_precond_apply")
+
+    def wcl_fermions_to_propagator(self, prop, x12):
+        """12 solutions [12][fermion] -> propagator [2][Lt][Lz][Ly][Lx/2][4][4][3][3]."""
+        import torch
+
+        n = self.fermion_numel * 12
+        _check(load_library().wcl_fermions_to_propagator(self.handle, _ptr(prop, torch.complex128, n, "prop", True),
+                                                         _ptr(x12, torch.complex128, n, "x12", True)),
+               "wcl_fermions_to_propagator")
+
+    def wcl_propagator_to_fermions(self, x12, prop):
+        import torch
+
+        n = self.fermion_numel * 12
+        _check(load_library().wcl_propagator_to_fermions(self.handle, _ptr(x12, torch.complex128, n, "x12", True),
+                                                         _ptr(prop, torch.complex128, n, "prop", True)),
+               "wcl_propagator_to_fermions")
 
     def wcl_precond_loss_grad(self, r_e, e_e, npairs: int):
         import numpy as np
