@@ -241,8 +241,8 @@ def test_propagator_layout_round_trip(pkg):
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     prop = cuda(np.zeros(shape[1:6] + (4, 4, 3, 3), dtype=np.complex128))
     ctx.wcl_fermions_to_propagator(prop, cuda(x))
-    ref = x.reshape((4, 3) + shape[1:]).transpose(2, 3, 4, 5, 6, 7, 0, 8, 1)  # [.., s0, c0 | s, c]
-    ref = ref.transpose(0, 1, 2, 3, 4, 6, 5, 8, 7)  # [.., s, s0, c, c0]
+    # axes of x as [s0, c0, parity, t, z, y, x/2, s, c] -> [parity, t, z, y, x/2, s, s0, c, c0]
+    ref = x.reshape((4, 3) + shape[1:]).transpose(2, 3, 4, 5, 6, 7, 0, 8, 1)
     assert np.array_equal(host(prop), ref)
     back = cuda(np.zeros_like(x))
     ctx.wcl_propagator_to_fermions(back, prop)
