@@ -530,7 +530,9 @@ struct CloverIO<DF64> {
   using R = dfloat;
   __device__ static void apply(cpx<R> y[12], const cpx<R> x[12], const void* base, const float*, long stride, long i) {
     const float4* p = static_cast<const float4*>(base);
-#pragma unroll
+    // one copy of the block multiply (code size: the double-float kernels are
+    // bound by instruction fetch when fully unrolled)
+#pragma unroll 1
     for (int b = 0; b < 2; b++) {
       R d[6];
       cpx<R> L[15];
