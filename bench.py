@@ -566,14 +566,13 @@ def run_precond_case(args):
 
     import workloads as W
     import __graft_entry__
-    from oracle import ptc
 
     __graft_entry__.build()
     import paper_2411_08461_gb300 as pkg
 
     dims = tuple(int(v) for v in args.lattice.split(","))
     ctx = _ctx_for(pkg, dims, SEED, torch.device("cuda", 0))
-    ctx.wcl_precond_load(pkg.ptc_flatten(ptc.init_weights(seed=1, scale=0.3)))
+    ctx.wcl_precond_load(pkg.ptc_flatten(W.ptc_weights(pkg.wcl.PTC_CHANNELS, seed=1, scale=0.3)))
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     r = torch.from_numpy(W.gaussian_fermion(dims, 2, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(args.nrhs, vh * 12)
     z = torch.empty_like(r)

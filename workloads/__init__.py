@@ -156,3 +156,14 @@ def random_su3(dims, seed: int) -> np.ndarray:
     r = rng.standard_normal((lt, lz, ly, lx, 8))
     return _su3_from_generators(r, 2.0)
 
+
+
+def ptc_weights(channels, seed: int, scale: float, nshift: int = 9) -> list[np.ndarray]:
+    """Random complex weights of a PTC network with the given channel counts: one
+    array [c_out][c_in][nshift][4][4] per layer, real and imaginary parts N(0, scale^2)."""
+    rng = np.random.default_rng(seed)
+    ws = []
+    for cin, cout in zip(channels[:-1], channels[1:]):
+        shape = (cout, cin, nshift, 4, 4)
+        ws.append(scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)))
+    return ws
