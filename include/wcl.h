@@ -228,6 +228,50 @@ wcl_status wcl_precond_train(wcl_ctx* ctx, const void* d_r_e, const void* d_e_e,
 wcl_status wcl_fermions_to_propagator(wcl_ctx* ctx, void* d_prop, const void* d_x12);
 wcl_status wcl_propagator_to_fermions(wcl_ctx* ctx, void* d_x12, const void* d_prop);
 
+/* ---- Propagator workflow around the solve (Sec. III.A, III.B) ----------------
+ * Momentum modes n = mom[0..2] (x, y, z; NULL = zero momentum) give
+ * p_k = 2 pi n_k / L_k.  A momentum source carries exp(+i p.x) and the sink of a
+ * contraction or a sequential source exp(-i p.x), the source and sink phases of
+ * Eq. 1 and Eq. 2.  Gamma arguments are host arrays of 16 complex entries (32
+ * doubles, row-major, re then im) with exactly one nonzero entry per row equal to
+ * 1, i, -1 or -i (within 1e-12): every product of DeGrand-Rossi gamma matrices,
+ * see wcl_gamma; anything else is WCL_ERR_INVALID_ARG.  Buffers are caller-owned
+ * device or page-locked host memory, complex128, QDP layout. */
+
+/* Gamma(n) = gamma_1^b0 gamma_2^b1 gamma_3^b2 gamma_4^b3 (b_k the bits of n, 0..15)
+ * in the DeGrand-Rossi basis (Sec. II.A; Gamma(15) = gamma_5, Gamma(4) = gamma_3,
+ * so Eq. 7's insertion is Gamma(15) Gamma(4)).  h_out: 32 doubles.  Host only: needs
+ * no context and no GPU. */
+wcl_status wcl_gamma(int n, double* h_out);
+
+/* kappa = 1 / (2 (m0 + 4)): the relation under Eq. 5 with xi_0 = nu = 1 (isotropic).
+ * Host only; WCL_ERR_INVALID_ARG unless m0 is finite and m0 > -4. */
+wcl_status wcl_kappa_from_mass(double m0, double* kappa);
+
+/* The twelve spin-colour wall sources on timeslice t0 (Sec. III.B): d_b12 is
+ * [12][fermion]; fermion k = 3 s + c is exp(+i p.x) (1 at zero momentum) in spin s,
+ * colour c on timeslice t0 and zero elsewhere -- the input of wcl_invert with
+ * nrhs = 12 for the propagator S_{p, t0} of Eq. 2. */
+wcl_status wcl_wall_source(wcl_ctx* ctx, void* d_b12, int t0, const int* mom);
+
+/* Sequential source (Eq. 4 and the sequential-source equation of Sec. III.B):
+ * X[site][i][k][a][b] = exp(-i p.x) sum_j Gamma[i][j] S[site][j][k][a][b] on timeslice
+ * t and zero elsewhere; d_X and d_S are propagators (distinct buffers), h_gamma NULL
+ * means gamma_5.  Invert its twelve source columns (wcl_propagator_to_fermions,
+ * wcl_invert) for the sequential propagator. */
+wcl_status wcl_sequential_source(wcl_ctx* ctx, void* d_X, const void* d_S, int t, const int* mom,
+                                 const double* h_gamma);
+
+/* Meson contraction (Eq. 6, Eq. 7): for every timeslice t,
+ *   out[t] = sum_{x in t} exp(-i p.x) sum_{i,j,k,a,b} conj(A[x][j][i][b][a]) Gamma[j][k] B[x][k][i][b][a]
+ * with A, B propagators and h_gamma NULL meaning the identity.  Eq. 6 is
+ * (A, B, Gamma, p) = (S_0, S_p, 1, p); Eq. 7 is (S_seq, S_p, gamma_5 gamma_3, 0).
+ * d_A, d_B: device memory (read with asynchronous shared-memory copies); d_out: Lt
+ * complex128, device or page-locked host.  Sums are FP64, added in a fixed order
+ * (deterministic). */
+wcl_status wcl_contract(wcl_ctx* ctx, void* d_out, const void* d_A, const void* d_B, const double* h_gamma,
+                        const int* mom);
+
 /* Options of a context (wcl_set_option). */
 typedef enum {
   WCL_OPT_TENSOR_CORES = 1 /* 1: 16-bit multi-RHS dslash (4..16 RHS) with the link and clover

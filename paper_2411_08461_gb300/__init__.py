@@ -12,7 +12,9 @@ from .wcl import (  # noqa: F401
     ptc_flatten,
     ptc_unflatten,
     wcl_default_train_params,
+    wcl_gamma,
     wcl_invert_batch,
+    wcl_kappa_from_mass,
     wcl_status_string,
 )
 

@@ -108,6 +108,11 @@ void free_lattice(wcl_ctx* c) {
 
 }  // namespace
 
+// fermion-style caller buffer (device or page-locked host) for the other translation units
+bool wcl_resolve_field(const wcl_ctx* c, const void* p, const void** out, const char* what) {
+  return field_ptr(c, p, out, what);
+}
+
 extern "C" {
 
 void wcl_default_params(wcl_solve_params* p) {

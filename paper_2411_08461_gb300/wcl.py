@@ -96,6 +96,12 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_double)]),
     "wcl_precond_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_train_params),
                                          ctypes.POINTER(ctypes.c_double)]),
+    "wcl_gamma": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "wcl_kappa_from_mass": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "wcl_wall_source": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "wcl_sequential_source": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "wcl_contract": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -155,6 +161,41 @@ def wcl_default_params(**overrides) -> wcl_solve_params:
 
 def wcl_status_string(status: int) -> str:
     return load_library().wcl_status_string(status).decode()
+
+
+def wcl_gamma(n: int):
+    """Gamma(n) in the DeGrand-Rossi basis as a 4 x 4 complex128 numpy array (host only)."""
+    import numpy as np
+
+    buf = np.zeros(32, dtype=np.float64)
+    _check(load_library().wcl_gamma(int(n), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "wcl_gamma")
+    return buf.view(np.complex128).reshape(4, 4)
+
+
+def wcl_kappa_from_mass(m0: float) -> float:
+    k = ctypes.c_double()
+    _check(load_library().wcl_kappa_from_mass(float(m0), ctypes.byref(k)), "wcl_kappa_from_mass")
+    return k.value
+
+
+def _mom_arg(mom):
+    if mom is None:
+        return None
+    if len(mom) != 3:
+        raise ValueError("mom must hold three integers (x, y, z)")
+    return (ctypes.c_int * 3)(*(int(v) for v in mom))
+
+
+def _gamma_arg(gamma):
+    import numpy as np
+
+    if gamma is None:
+        return None, None
+    g = np.ascontiguousarray(np.asarray(gamma, dtype=np.complex128))
+    if g.shape != (4, 4):
+        raise ValueError("gamma must be a 4 x 4 matrix")
+    buf = g.view(np.float64).ravel().copy()
+    return buf, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
 class Context:
@@ -267,6 +308,36 @@ class Context:
         _check(load_library().wcl_propagator_to_fermions(self.handle, _ptr(x12, torch.complex128, n, "x12", True),
                                                          _ptr(prop, torch.complex128, n, "prop", True)),
                "wcl_propagator_to_fermions")
+
+    def wcl_wall_source(self, b12, t0: int, mom=None):
+        """Twelve wall sources on timeslice t0 ([12][fermion]), momentum phase exp(+i p.x)."""
+        import torch
+
+        n = self.fermion_numel * 12
+        _check(load_library().wcl_wall_source(self.handle, _ptr(b12, torch.complex128, n, "b12", True), int(t0),
+                                              _mom_arg(mom)), "wcl_wall_source")
+
+    def wcl_sequential_source(self, X, S, t: int, mom=None, gamma=None):
+        """X = exp(-i p.x) Gamma S on timeslice t (Gamma = gamma_5 when None); propagators."""
+        import torch
+
+        n = self.fermion_numel * 12
+        keep, g = _gamma_arg(gamma)
+        _check(load_library().wcl_sequential_source(self.handle, _ptr(X, torch.complex128, n, "X", True),
+                                                    _ptr(S, torch.complex128, n, "S", True), int(t), _mom_arg(mom), g),
+               "wcl_sequential_source")
+        del keep
+
+    def wcl_contract(self, out, A, B, gamma=None, mom=None):
+        """out[t] = sum_{x in t} exp(-i p.x) conj(A) Gamma B summed over spin and colour (Lt complex128)."""
+        import torch
+
+        n = self.fermion_numel * 12
+        keep, g = _gamma_arg(gamma)
+        _check(load_library().wcl_contract(self.handle, _ptr(out, torch.complex128, self.dims[3], "out", True),
+                                           _ptr(A, torch.complex128, n, "A", True), _ptr(B, torch.complex128, n, "B", True), g,
+                                           _mom_arg(mom)), "wcl_contract")
+        del keep
 
     def wcl_precond_loss_grad(self, r_e, e_e, npairs: int):
         import numpy as np

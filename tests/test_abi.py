@@ -53,3 +53,26 @@ def test_host_only_calls_without_a_gpu():
     dims = (ctypes.c_int * 4)(3, 4, 4, 4)
     assert lib.wcl_create(ctypes.byref(h), dims, -1, 0, None) == 1
     assert b"even" in lib.wcl_last_error()
+
+
+def test_gamma_and_kappa_helpers_without_a_gpu():
+    """wcl_gamma reproduces the oracle's independently written Gamma(n) for all 16 n,
+    and wcl_kappa_from_mass the isotropic kappa relation; both are host-only calls."""
+    import numpy as np
+
+    import __graft_entry__
+    from oracle import gamma as G
+
+    __graft_entry__.build()
+    from paper_2411_08461_gb300 import wcl
+
+    for n in range(16):
+        np.testing.assert_array_equal(wcl.wcl_gamma(n), G.gamma(n))
+    assert np.array_equal(wcl.wcl_gamma(15) @ wcl.wcl_gamma(4), G.GAMMA5 @ G.GAMMA[2])
+    assert wcl.wcl_kappa_from_mass(0.0) == 0.125
+    assert abs(wcl.wcl_kappa_from_mass(-0.2770) - 1 / (2 * 3.723)) < 1e-15
+    for bad in (-4.0, -5.0, float("nan")):
+        with pytest.raises(wcl.WclError):
+            wcl.wcl_kappa_from_mass(bad)
+    with pytest.raises(wcl.WclError):
+        wcl.wcl_gamma(16)

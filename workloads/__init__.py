@@ -167,3 +167,20 @@ def ptc_weights(channels, seed: int, scale: float, nshift: int = 9) -> list[np.n
         shape = (cout, cin, nshift, 4, 4)
         ws.append(scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)))
     return ws
+
+
+def gaussian_propagator(dims, seed: int) -> np.ndarray:
+    """Gaussian propagator-shaped field, re and im ~ N(0,1), drawn in lexicographic
+    order; QDP layout [2][Lt][Lz][Ly][Lx/2][4][4][3][3]."""
+    lx, ly, lz, lt = _check_dims(dims)
+    z = np.random.default_rng(seed).standard_normal((lt, lz, ly, lx, 4, 4, 3, 3, 2))
+    return sites_to_cb2(z[..., 0] + 1j * z[..., 1], dims)
+
+
+def gaussian_propagator_runs(dims, t: int, seed: int) -> np.ndarray:
+    """Gaussian data for the two storage runs of timeslice t of a QDP propagator (the
+    sites of parity 0, then of parity 1, each in [Lz][Ly][Lx/2] order): shape
+    [2][Lz][Ly][Lx/2][4][4][3][3]."""
+    lx, ly, lz, lt = _check_dims(dims)
+    z = np.random.default_rng([seed, t]).standard_normal((2, lz, ly, lx // 2, 4, 4, 3, 3, 2))
+    return z[..., 0] + 1j * z[..., 1]
