@@ -58,10 +58,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairs", type=int, default=2000, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
-    ap.add_argument("--case", default="solve", choices=["solve", "mhat", "compare", "batch", "throughput", "precond"],
+    ap.add_argument("--case", default="solve",
+                    choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures); "
                          "batch: four uneven lattices x 12 Z2 sources in one batched solve vs single-RHS "
-                         "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve")
+                         "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve; "
+                         "propagator: the Sec. III.B sequence (wall propagators, sequential propagator, "
+                         "two- and three-point functions) on --dims, with the contraction kernel's roofline")
+    ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of --case propagator")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
     ap.add_argument("--dims", default="32,32,32,64", help="lattice of --case solve (the bench line uses 32^3x64)")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
@@ -594,6 +598,95 @@ def run_precond_case(args):
     return 0
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+
+
+def run_propagator_case(args):
+    """The Sec. III.B sequence on --dims with the FP32 mixed-precision 12-RHS solver
+    (FP64 reliable updates, tolerance --tol): wall sources at t0 = 0 with p = 0 and
+    p = (0, 0, 1), the two propagators, the sequential source at t = Lt/2, the
+    sequential propagator, the two-point (Eq. 6) and three-point (Eq. 7) functions.
+    Then --steps timed calls of each contraction (CUDA events, after --warmup) for the
+    contraction kernel's roofline: 4608 algorithmic bytes (two complex128
+    propagators) and 1152 FP64 flops (144 complex multiply-adds) per site."""
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    dims = tuple(int(v) for v in args.dims.split(","))
+    lx, ly, lz, lt = dims
+    V = lx * ly * lz * lt
+    t0, ts, mom = 0, lt // 2, (0, 0, 1)
+    ctx = _ctx_for(pkg, dims, SEED, dev)
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=args.tol, check_every=args.check_every,
+                                 delta_reliable=args.delta)
+    f12 = lambda: torch.zeros((12, V * 12), dtype=torch.complex128, device=dev)
+    b0, bp, x, S0, Sp, X, Sseq = f12(), f12(), f12(), f12(), f12(), f12(), f12()
+    two = torch.zeros(lt, dtype=torch.complex128, device=dev)
+    three = torch.zeros_like(two)
+    g53 = pkg.wcl_gamma(15) @ pkg.wcl_gamma(4)
+    ctx.wcl_wall_source(b0, t0)
+    ctx.wcl_invert(x, b0, 12, prm)  # warm-up: tuning and graph capture
+    torch.cuda.synchronize()
+    iters = []
+
+    def solve_into(prop, b):
+        x.zero_()
+        _, info = ctx.wcl_invert(x, b, 12, prm)
+        iters.append(max(i["iters"] for i in info))
+        assert all(i["true_residual"] <= args.tol for i in info), info
+        ctx.wcl_fermions_to_propagator(prop, x)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.wcl_wall_source(b0, t0)
+    ctx.wcl_wall_source(bp, t0, mom)
+    solve_into(S0, b0)
+    solve_into(Sp, bp)
+    ctx.wcl_sequential_source(X, S0, ts, mom)
+    ctx.wcl_propagator_to_fermions(b0, X)
+    solve_into(Sseq, b0)
+    ctx.wcl_contract(two, S0, Sp, None, mom)
+    ctx.wcl_contract(three, Sseq, Sp, g53)
+    e1.record()
+    torch.cuda.synchronize()
+    workflow_s = e0.elapsed_time(e1) / 1e3
+
+    timings = {}
+    for name, call in (("two_point", lambda: ctx.wcl_contract(two, S0, Sp, None, mom)),
+                       ("three_point", lambda: ctx.wcl_contract(three, Sseq, Sp, g53))):
+        for _ in range(max(3, args.warmup)):
+            call()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        timings[name] = e0.elapsed_time(e1) / args.steps
+    peak, kind = measured_peaks()
+    byts, flops = 4608.0 * V, 1152.0 * V
+    roof = {}
+    for name, ms in timings.items():
+        gbs = byts / (ms * 1e-3) / 1e9
+        tfl = flops / (ms * 1e-3) / 1e12
+        roof[name] = {"ms_per_call": ms, "gbs": gbs, "hbm_frac": gbs / peak, "fp64_tflops": tfl,
+                      "fp64_frac": tfl / FP64_NOMINAL_TFLOPS}
+    print(json.dumps({"case": "propagator", "lattice": dims, "tol": args.tol, "sloppy": args.sloppy,
+                      "workflow_s": workflow_s, "max_iters_per_solve": iters,
+                      "two_point": [[c.real, c.imag] for c in two.cpu().tolist()[:4]],
+                      "contraction": roof, "hbm_peak_gbs": peak, "hbm_peak_kind": kind,
+                      "fp64_peak_tflops": FP64_NOMINAL_TFLOPS, "fp64_peak_kind": "nominal",
+                      "note": "each contraction call includes its finaliser and, with momentum, the phase table"}))
+    ctx.close()
+    return 0
+
+
 def run_compare_case(args):
     """12 point sources on 32^3x64 solved four ways, each to a 1e-10 true residual:
     plain FP32 single-RHS BiCGStab (12 sequential solves, FP64 restarts), the
@@ -714,6 +807,8 @@ def main():
         return run_compare_case(args)
     if args.case == "precond":
         return run_precond_case(args)
+    if args.case == "propagator":
+        return run_propagator_case(args)
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores only; other ranks exit without work
         return run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
