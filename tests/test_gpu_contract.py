@@ -33,7 +33,8 @@ def _ctx(pkg, dims):
 
 
 def _lex_prop(qdp, dims):
-    return L.from_qdp(qdp, dims)
+    lx, ly, lz, lt = dims
+    return L.from_qdp(qdp.reshape((2, lt, lz, ly, lx // 2, 4, 4, 3, 3)), dims)
 
 
 @pytest.mark.parametrize("dims", SHAPES)
