@@ -468,6 +468,10 @@ wcl_status wcl_contract(wcl_ctx* c, void* d_out, const void* d_A, const void* d_
     count_launch(c);
     a.ph = static_cast<const double2*>(ph);
   }
+  // the one-warp CTAs are bounded by shared memory: ask for the largest carveout so
+  // that five fit on an SM
+  WCL_CUDA(cudaFuncSetAttribute(contract_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared));
   contract_kernel<<<dim3(a.chunks, 2 * g.Lt), 32, CT_SMEM, c->stream>>>(a);
   WCL_CUDA(cudaGetLastError());
   count_launch(c);
