@@ -209,21 +209,24 @@ __global__ void __launch_bounds__(32) contract_kernel(ContractArgs a) {
     if (first + s < a.vs2) {
       const double2* sa = ct_smem + (tl & 1) * CT_STAGE + s * CT_ROW + i * 9;
       const double2* sb = sa + CT_SITES * CT_ROW;
-      double xr0 = 0.0, xi0 = 0.0, xr1 = 0.0, xi1 = 0.0;
+      // eight independent FMA chains (re*re, im*im, re*im, im*re of both rows): the
+      // dependent-FMA latency, not the FP64 pipe, bounded a four-chain form
+      double rr0 = 0.0, ii0 = 0.0, ri0 = 0.0, ir0 = 0.0, rr1 = 0.0, ii1 = 0.0, ri1 = 0.0, ir1 = 0.0;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         const double2 a0 = sa[j0 * 36 + m], b0 = sb[c0 * 36 + m];
         const double2 a1 = sa[j1 * 36 + m], b1 = sb[c1 * 36 + m];
-        xr0 = fma(a0.x, b0.x, xr0);
-        xr0 = fma(a0.y, b0.y, xr0);
-        xi0 = fma(a0.x, b0.y, xi0);
-        xi0 = fma(-a0.y, b0.x, xi0);
-        xr1 = fma(a1.x, b1.x, xr1);
-        xr1 = fma(a1.y, b1.y, xr1);
-        xi1 = fma(a1.x, b1.y, xi1);
-        xi1 = fma(-a1.y, b1.x, xi1);
+        rr0 = fma(a0.x, b0.x, rr0);
+        ii0 = fma(a0.y, b0.y, ii0);
+        ri0 = fma(a0.x, b0.y, ri0);
+        ir0 = fma(a0.y, b0.x, ir0);
+        rr1 = fma(a1.x, b1.x, rr1);
+        ii1 = fma(a1.y, b1.y, ii1);
+        ri1 = fma(a1.x, b1.y, ri1);
+        ir1 = fma(a1.y, b1.x, ir1);
       }
-      const double2 u0 = rot_i(make_double2(xr0, xi0), r0), u1 = rot_i(make_double2(xr1, xi1), r1);
+      const double2 u0 = rot_i(make_double2(rr0 + ii0, ri0 - ir0), r0);
+      const double2 u1 = rot_i(make_double2(rr1 + ii1, ri1 - ir1), r1);
       const double ur = u0.x + u1.x, ui = u0.y + u1.y;
       if (a.ph) {
         const double2 p = a.ph[run_base + first + s];
