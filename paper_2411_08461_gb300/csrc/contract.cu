@@ -145,17 +145,20 @@ __global__ void phase_table_kernel(double2* __restrict__ ph, SiteGeom g, Mom m) 
 }
 
 // ---- contraction ------------------------------------------------------------------
-// One warp per CTA.  A run is the contiguous storage range of one (parity, timeslice);
-// a CTA takes `tiles_per_block` consecutive tiles of CT_SITES sites from one run and
-// double-buffers them in shared memory with cp.async (16-byte copies, coalesced).
-// Lane (h, s, i) then reads rows 2h and 2h+1 of site s, source spin i: nine
-// colour pairs each of A and of the B row that Gamma selects (padded site rows keep
-// the 16-byte shared-memory reads conflict-free).  Each CTA writes one partial sum;
-// the finaliser adds them per timeslice in a fixed order (deterministic).
+// A run is the contiguous storage range of one (parity, timeslice).  A CTA takes
+// `tiles_per_block` consecutive tiles of CT_SITES sites from one run; each of its
+// CT_WARPS warps owns one shared-memory stage and loads its tiles into it with
+// cp.async (16-byte copies, coalesced), single-buffered: the warps of the SM (twelve
+// at 38 KB per CTA) hide each other's loads.  Lane (h, s, i) then reads rows 2h and
+// 2h+1 of site s, source spin i: nine colour pairs each of A and of the B row that
+// Gamma selects (padded site rows keep the 16-byte shared-memory reads conflict-free).
+// Each CTA writes one partial sum; the finaliser adds them per timeslice in a fixed
+// order (deterministic).
 constexpr int CT_SITES = 4;
 constexpr int CT_ROW = 148;                          // double2 per staged site: 144 + 4 padding
 constexpr int CT_STAGE = 2 * CT_SITES * CT_ROW;      // A and B of one tile
-constexpr size_t CT_SMEM = 2 * CT_STAGE * sizeof(double2);
+constexpr int CT_WARPS = 2;
+constexpr size_t CT_SMEM = CT_WARPS * CT_STAGE * sizeof(double2);
 
 struct ContractArgs {
   const double2* A;
@@ -181,9 +184,11 @@ __device__ __forceinline__ void contract_issue(const ContractArgs& a, double2* d
   cp_async_commit();
 }
 
-__global__ void __launch_bounds__(32) contract_kernel(ContractArgs a) {
+__global__ void __launch_bounds__(32 * CT_WARPS) contract_kernel(ContractArgs a) {
   extern __shared__ double2 ct_smem[];
-  const int lane = threadIdx.x;
+  __shared__ double2 warp_sum[CT_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double2* stage = ct_smem + warp * CT_STAGE;
   const int run = blockIdx.y;
   const int par = run / a.lt, t = run - par * a.lt;
   const long run_base = (long)par * a.vh + (long)t * a.vs2;
@@ -196,37 +201,29 @@ __global__ void __launch_bounds__(32) contract_kernel(ContractArgs a) {
   const int r0 = h ? a.gr.rot[2] : a.gr.rot[0], r1 = h ? a.gr.rot[3] : a.gr.rot[1];
 
   double tr = 0.0, ti = 0.0;
-  if (ntile > 0) contract_issue(a, ct_smem, run_base, tile0 * CT_SITES, lane);
-  for (int tl = 0; tl < ntile; tl++) {
-    if (tl + 1 < ntile) {
-      contract_issue(a, ct_smem + ((tl + 1) & 1) * CT_STAGE, run_base, (tile0 + tl + 1) * CT_SITES, lane);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncwarp();
+  for (int tl = warp; tl < ntile; tl += CT_WARPS) {
     const int first = (tile0 + tl) * CT_SITES;
+    contract_issue(a, stage, run_base, first, lane);
+    cp_async_wait<0>();
+    __syncwarp();
     if (first + s < a.vs2) {
-      const double2* sa = ct_smem + (tl & 1) * CT_STAGE + s * CT_ROW + i * 9;
+      const double2* sa = stage + s * CT_ROW + i * 9;
       const double2* sb = sa + CT_SITES * CT_ROW;
-      // eight independent FMA chains (re*re, im*im, re*im, im*re of both rows): the
-      // dependent-FMA latency, not the FP64 pipe, bounded a four-chain form
-      double rr0 = 0.0, ii0 = 0.0, ri0 = 0.0, ir0 = 0.0, rr1 = 0.0, ii1 = 0.0, ri1 = 0.0, ir1 = 0.0;
+      double xr0 = 0.0, xi0 = 0.0, xr1 = 0.0, xi1 = 0.0;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         const double2 a0 = sa[j0 * 36 + m], b0 = sb[c0 * 36 + m];
         const double2 a1 = sa[j1 * 36 + m], b1 = sb[c1 * 36 + m];
-        rr0 = fma(a0.x, b0.x, rr0);
-        ii0 = fma(a0.y, b0.y, ii0);
-        ri0 = fma(a0.x, b0.y, ri0);
-        ir0 = fma(a0.y, b0.x, ir0);
-        rr1 = fma(a1.x, b1.x, rr1);
-        ii1 = fma(a1.y, b1.y, ii1);
-        ri1 = fma(a1.x, b1.y, ri1);
-        ir1 = fma(a1.y, b1.x, ir1);
+        xr0 = fma(a0.x, b0.x, xr0);
+        xr0 = fma(a0.y, b0.y, xr0);
+        xi0 = fma(a0.x, b0.y, xi0);
+        xi0 = fma(-a0.y, b0.x, xi0);
+        xr1 = fma(a1.x, b1.x, xr1);
+        xr1 = fma(a1.y, b1.y, xr1);
+        xi1 = fma(a1.x, b1.y, xi1);
+        xi1 = fma(-a1.y, b1.x, xi1);
       }
-      const double2 u0 = rot_i(make_double2(rr0 + ii0, ri0 - ir0), r0);
-      const double2 u1 = rot_i(make_double2(rr1 + ii1, ri1 - ir1), r1);
+      const double2 u0 = rot_i(make_double2(xr0, xi0), r0), u1 = rot_i(make_double2(xr1, xi1), r1);
       const double ur = u0.x + u1.x, ui = u0.y + u1.y;
       if (a.ph) {
         const double2 p = a.ph[run_base + first + s];
@@ -237,14 +234,20 @@ __global__ void __launch_bounds__(32) contract_kernel(ContractArgs a) {
         ti += ui;
       }
     }
-    __syncwarp();  // every lane is done with this stage before it is refilled
+    __syncwarp();  // every lane is done with the stage before it is refilled
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     tr += __shfl_xor_sync(0xffffffffu, tr, o);
     ti += __shfl_xor_sync(0xffffffffu, ti, o);
   }
-  if (lane == 0) a.partials[(long)run * a.chunks + blockIdx.x] = make_double2(tr, ti);
+  if (lane == 0) warp_sum[warp] = make_double2(tr, ti);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 v = warp_sum[0];
+    for (int w = 1; w < CT_WARPS; w++) v.x += warp_sum[w].x, v.y += warp_sum[w].y;
+    a.partials[(long)run * a.chunks + blockIdx.x] = v;
+  }
 }
 
 // out[t] = sum over both parities and every chunk of the partials of timeslice t
@@ -471,11 +474,11 @@ wcl_status wcl_contract(wcl_ctx* c, void* d_out, const void* d_A, const void* d_
     count_launch(c);
     a.ph = static_cast<const double2*>(ph);
   }
-  // the one-warp CTAs are bounded by shared memory: ask for the largest carveout so
-  // that five fit on an SM
+  // the CTAs are bounded by shared memory: ask for the largest carveout so that six
+  // fit on an SM
   WCL_CUDA(cudaFuncSetAttribute(contract_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 cudaSharedmemCarveoutMaxShared));
-  contract_kernel<<<dim3(a.chunks, 2 * g.Lt), 32, CT_SMEM, c->stream>>>(a);
+  contract_kernel<<<dim3(a.chunks, 2 * g.Lt), 32 * CT_WARPS, CT_SMEM, c->stream>>>(a);
   WCL_CUDA(cudaGetLastError());
   count_launch(c);
   contract_finalize_kernel<<<g.Lt, 256, 0, c->stream>>>(static_cast<double2*>(const_cast<void*>(po)), a.partials,
