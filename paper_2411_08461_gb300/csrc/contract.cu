@@ -149,7 +149,7 @@ __global__ void phase_table_kernel(double2* __restrict__ ph, SiteGeom g, Mom m) 
 // `tiles_per_block` consecutive tiles of CT_SITES sites from one run; each of its
 // CT_WARPS warps owns one shared-memory stage and loads its tiles into it with
 // cp.async (16-byte copies, coalesced), single-buffered: the warps of the SM (twelve
-// at 38 KB per CTA) hide each other's loads.  Lane (h, s, i) then reads rows 2h and
+// at 37 KB per CTA) hide each other's loads.  Lane (h, s, i) then reads rows 2h and
 // 2h+1 of site s, source spin i: nine colour pairs each of A and of the B row that
 // Gamma selects (padded site rows keep the 16-byte shared-memory reads conflict-free).
 // Each CTA writes one partial sum; the finaliser adds them per timeslice in a fixed
@@ -186,7 +186,6 @@ __device__ __forceinline__ void contract_issue(const ContractArgs& a, double2* d
 
 __global__ void __launch_bounds__(32 * CT_WARPS) contract_kernel(ContractArgs a) {
   extern __shared__ double2 ct_smem[];
-  __shared__ double2 warp_sum[CT_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double2* stage = ct_smem + warp * CT_STAGE;
   const int run = blockIdx.y;
@@ -241,11 +240,13 @@ __global__ void __launch_bounds__(32 * CT_WARPS) contract_kernel(ContractArgs a)
     tr += __shfl_xor_sync(0xffffffffu, tr, o);
     ti += __shfl_xor_sync(0xffffffffu, ti, o);
   }
-  if (lane == 0) warp_sum[warp] = make_double2(tr, ti);
+  // each warp leaves its sum in the first slot of its own (now idle) stage: no static
+  // shared memory, so six CTAs still fit on an SM
+  if (lane == 0) stage[0] = make_double2(tr, ti);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double2 v = warp_sum[0];
-    for (int w = 1; w < CT_WARPS; w++) v.x += warp_sum[w].x, v.y += warp_sum[w].y;
+    double2 v = ct_smem[0];
+    for (int w = 1; w < CT_WARPS; w++) v.x += ct_smem[w * CT_STAGE].x, v.y += ct_smem[w * CT_STAGE].y;
     a.partials[(long)run * a.chunks + blockIdx.x] = v;
   }
 }
