@@ -22,9 +22,16 @@ Because H only couples nearest neighbours, H of a field supported on one
 parity is supported on the other; the oracle therefore keeps whole-lattice
 arrays and lets the parity of the support select D_eo or D_oe.
 
-Pins (tests/test_oracle_dirac.py): free-field plane waves, gamma_5-hermiticity,
-gauge covariance, the abelian constant-field clover, and a loop-built dense
-matrix on 2^4.
+Anisotropic form (Eq. 5 with general xi_0, nu, c_SW^t, c_SW^r), through
+``anisotropic``: the spatial hops carry nu/xi_0, the clover planes (i, 4) carry
+c_SW^t and the planes (i, j) carry c_SW^r/xi_0, and kappa^-1 = 2 (m0 + 1 + 3 nu/xi_0)
+(``kappa_of_mass``).  The isotropic operator is the case xi_0 = nu = 1,
+c_SW^t = c_SW^r = c_sw.
+
+Pins (tests/test_oracle_dirac.py): free-field plane waves (isotropic and
+anisotropic), the massless point of the kappa relation, gamma_5-hermiticity,
+gauge covariance, the abelian constant-field clover in a spatial and a temporal
+plane, and a loop-built dense matrix on 2^4 and small anisotropic lattices.
 """
 import numpy as np
 
@@ -52,8 +59,10 @@ def _spin(g, psi):
     return np.einsum("st,...tc->...sc", g, psi)
 
 
-def hopping(U: np.ndarray, psi: np.ndarray, t_boundary: int = -1, dagger: bool = False) -> np.ndarray:
-    """H psi, or H^+ psi = gamma5 H gamma5 psi (projector signs swapped) when dagger is set."""
+def hopping(U: np.ndarray, psi: np.ndarray, t_boundary: int = -1, dagger: bool = False,
+            weights=None) -> np.ndarray:
+    """H psi, or H^+ psi = gamma5 H gamma5 psi (projector signs swapped) when dagger is set.
+    weights: optional factor per direction mu (the nu/xi_0 of Eq. 5's spatial hops)."""
     dims = L.dims_of(psi)
     out = np.zeros_like(psi)
     sgn = -1.0 if dagger else 1.0
@@ -63,7 +72,8 @@ def hopping(U: np.ndarray, psi: np.ndarray, t_boundary: int = -1, dagger: bool =
         if mu == 3:
             f = f * L.time_boundary_sign(dims, t_boundary, True)[..., None, None]
             b = b * L.time_boundary_sign(dims, t_boundary, False)[..., None, None]
-        out += _spin(ID4 - sgn * GAMMA[mu], f) + _spin(ID4 + sgn * GAMMA[mu], b)
+        term = _spin(ID4 - sgn * GAMMA[mu], f) + _spin(ID4 + sgn * GAMMA[mu], b)
+        out += term if weights is None else weights[mu] * term
     return out
 
 
@@ -87,12 +97,19 @@ def field_strength(U: np.ndarray, mu: int, nu: int) -> np.ndarray:
     return f - tr[..., None, None] / 3.0 * np.eye(3)
 
 
-def clover_matrix(U: np.ndarray, kappa: float, csw: float) -> np.ndarray:
+def clover_matrix(U: np.ndarray, kappa: float, csw: float, plane_csw=None) -> np.ndarray:
     """A(s) = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(s), as 12x12 per site.
 
-    Row/column index is 3*spin + colour.
+    Row/column index is 3*spin + colour.  plane_csw: optional coefficient per plane
+    of PLANES replacing c_sw (Eq. 5's c_SW^t on (i, 4), c_SW^r/xi_0 on (i, j)).
     """
     site_shape = U.shape[1:5]
+    if plane_csw is not None:
+        a = np.zeros(site_shape + (12, 12), dtype=np.complex128)
+        for (mu, nu), c in zip(PLANES, plane_csw):
+            fmn = field_strength(U, mu, nu)
+            a += c * np.einsum("st,...ab->...satb", sigma(mu, nu), fmn).reshape(site_shape + (12, 12))
+        return np.eye(12) - kappa * a
     a = np.zeros(site_shape + (12, 12), dtype=np.complex128)
     for mu, nu in PLANES:
         fmn = field_strength(U, mu, nu)
@@ -114,20 +131,22 @@ def gamma5(psi: np.ndarray) -> np.ndarray:
 class WilsonClover:
     """The operator M = A - kappa H of one gauge field, with its even-odd pieces."""
 
-    def __init__(self, U: np.ndarray, kappa: float, csw: float, t_boundary: int = -1):
+    def __init__(self, U: np.ndarray, kappa: float, csw: float, t_boundary: int = -1, hop_weights=None,
+                 plane_csw=None):
         self.U = U
         self.kappa = float(kappa)
         self.csw = float(csw)
         self.t_boundary = int(t_boundary)
+        self.hop_weights = hop_weights
         self.dims = (U.shape[4], U.shape[3], U.shape[2], U.shape[1])
-        self.A = clover_matrix(U, kappa, csw)
+        self.A = clover_matrix(U, kappa, csw, plane_csw)
         self.Ainv = np.linalg.inv(self.A)
         self.even = L.parity_mask(self.dims, 0)[..., None, None]
         self.odd = ~self.even
 
     # full operator ---------------------------------------------------------
     def H(self, psi, dagger=False):
-        return hopping(self.U, psi, self.t_boundary, dagger)
+        return hopping(self.U, psi, self.t_boundary, dagger, self.hop_weights)
 
     def M(self, psi):
         """M psi = A psi - kappa H psi on the whole lattice."""
@@ -158,6 +177,20 @@ class WilsonClover:
     def true_residual(self, x, b) -> float:
         """||b - M x||_2 / ||b||_2 over the whole lattice: the relative true residual of the full system."""
         return float(np.linalg.norm(b - self.M(x)) / np.linalg.norm(b))
+
+
+def anisotropic(U, kappa, xi0, nu, csw_t, csw_r, t_boundary=-1) -> WilsonClover:
+    """Eq. 5 with anisotropy: 2 kappa a_t M = 1 - kappa [gamma_4 W_4 + (nu/xi_0) sum_i gamma_i W_i
+    + c_SW^t sum_i sigma_{i4} F_{i4} + (c_SW^r/xi_0) sum_{i<j} sigma_{ij} F_{ij}], with the
+    hopping read as for the isotropic operator (Wilson r = 1 projectors)."""
+    w = nu / xi0
+    plane_csw = [csw_t if nu_ == 3 else csw_r / xi0 for _, nu_ in PLANES]
+    return WilsonClover(U, kappa, 0.0, t_boundary, hop_weights=(w, w, w, 1.0), plane_csw=plane_csw)
+
+
+def kappa_of_mass(m0, xi0=1.0, nu=1.0):
+    """kappa^-1 = 2 (m0 + 1 + 3 nu/xi_0), the relation stated under Eq. 5."""
+    return 1.0 / (2.0 * (m0 + 1.0 + 3.0 * nu / xi0))
 
 
 # QDP-layout conveniences used by the tests -------------------------------------

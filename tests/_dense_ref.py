@@ -59,7 +59,10 @@ def leaf_sum(U, c, mu, nu, dims):
             + walk([(nu, -1), (mu, 1), (nu, 1), (mu, -1)]))
 
 
-def dense_matrix(U, dims, kappa, csw, t_boundary=-1):
+def dense_matrix(U, dims, kappa, csw, t_boundary=-1, aniso=None):
+    """Eq. 5; aniso = (xi0, nu, csw_t, csw_r) gives the anisotropic form: spatial hops
+    times nu/xi0, clover planes containing t times csw_t, purely spatial planes times
+    csw_r/xi0 (csw unused)."""
     lx, ly, lz, lt = dims
     V = lx * ly * lz * lt
     M = np.zeros((12 * V, 12 * V), dtype=np.complex128)
@@ -74,7 +77,11 @@ def dense_matrix(U, dims, kappa, csw, t_boundary=-1):
                 f = (q - q.conj().T) / 8.0
                 f = f - np.trace(f) / 3.0 * np.eye(3)
                 sig = 0.5 * (GAMMA[mu] @ GAMMA[nu] - GAMMA[nu] @ GAMMA[mu])
-                a -= kappa * csw * np.kron(sig, f)
+                if aniso is None:
+                    coef = csw
+                else:
+                    coef = aniso[2] if nu == 3 else aniso[3] / aniso[0]
+                a -= kappa * coef * np.kron(sig, f)
         M[12 * i:12 * i + 12, 12 * i:12 * i + 12] += a
         # hopping: forward and backward in every direction
         for mu in range(4):
@@ -82,6 +89,8 @@ def dense_matrix(U, dims, kappa, csw, t_boundary=-1):
             cb = step(c, mu, -1, dims)
             sf = t_boundary if (mu == 3 and c[3] == lt - 1) else 1.0
             sb = t_boundary if (mu == 3 and c[3] == 0) else 1.0
+            if aniso is not None and mu < 3:
+                sf, sb = sf * aniso[1] / aniso[0], sb * aniso[1] / aniso[0]
             jf, jb = site_index(cf, dims), site_index(cb, dims)
             M[12 * i:12 * i + 12, 12 * jf:12 * jf + 12] += -kappa * sf * np.kron(one - GAMMA[mu], link(U, c, mu))
             M[12 * i:12 * i + 12, 12 * jb:12 * jb + 12] += -kappa * sb * np.kron(one + GAMMA[mu], link(U, cb, mu).conj().T)

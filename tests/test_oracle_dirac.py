@@ -192,3 +192,87 @@ def test_site_by_site_schur_operator_matches_whole_lattice(dagger):
     vals = dirac.Mhat_at_sites(gq, xe, dims, 0.127, 1.3, sites, dagger=dagger)
     for (x, y, z, t), v in zip(sites, vals):
         np.testing.assert_allclose(v, ref[t, z, y, x], atol=1e-13)
+
+
+# --- anisotropic form of Eq. 5 --------------------------------------------------
+
+ANISO = dict(xi0=2.464, nu=0.95, csw_t=0.91, csw_r=1.07)  # the parameters of the Sec. III.B example
+
+
+def test_anisotropic_reduces_to_isotropic():
+    dims = (4, 2, 2, 4)
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.5, 31), dims)
+    psi = _rand_fermion(dims, 32)
+    iso = dirac.WilsonClover(U, 0.12, 1.3)
+    an = dirac.anisotropic(U, 0.12, 1.0, 1.0, 1.3, 1.3)
+    np.testing.assert_allclose(an.M(psi), iso.M(psi), atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [(0, 0, 0, 0), (1, 0, 2, 1), (1, 1, 1, 3)])
+def test_anisotropic_free_field_plane_wave(n):
+    """Unit links: M e^{ipx} u = [1 - kappa sum_mu w_mu (2 cos p_mu - 2 i gamma_mu sin p_mu)] e^{ipx} u
+    with w = nu/xi0 on the spatial directions and 1 on t."""
+    dims = (4, 2, 6, 8)
+    kappa = 0.09
+    U = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    op = dirac.anisotropic(U, kappa, **ANISO)
+    lx, ly, lz, lt = dims
+    p = [2 * np.pi * n[0] / lx, 2 * np.pi * n[1] / ly, 2 * np.pi * n[2] / lz, (2 * np.pi * n[3] + np.pi) / lt]
+    w = [ANISO["nu"] / ANISO["xi0"]] * 3 + [1.0]
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    u = np.random.default_rng(3).standard_normal((4, 3)) + 0j
+    Mp = (1 - 2 * kappa * sum(w[m] * np.cos(p[m]) for m in range(4))) * np.eye(4) + 2j * kappa * sum(
+        w[m] * GAMMA[m] * np.sin(p[m]) for m in range(4))
+    np.testing.assert_allclose(op.M(phase[..., None, None] * u), phase[..., None, None] * (Mp @ u), atol=1e-13)
+
+
+def test_kappa_relation_massless_point():
+    """kappa from m0 = 0 puts the free operator's zero-momentum mode at zero (periodic t)."""
+    dims = (2, 2, 2, 4)
+    U = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    for xi0, nu in ((1.0, 1.0), (ANISO["xi0"], ANISO["nu"])):
+        k0 = dirac.kappa_of_mass(0.0, xi0, nu)
+        op = dirac.anisotropic(U, k0, xi0, nu, 1.0, 1.0, t_boundary=1)
+        const = np.ones(op.dims[::-1] + (4, 3), dtype=np.complex128)
+        assert np.abs(op.M(const)).max() < 1e-14
+        m0 = 0.3
+        k = dirac.kappa_of_mass(m0, xi0, nu)
+        np.testing.assert_allclose(dirac.anisotropic(U, k, xi0, nu, 1.0, 1.0, 1).M(const), 2 * k * m0 * const,
+                                   atol=1e-14)
+    assert dirac.kappa_of_mass(0.0) == 0.125
+
+
+@pytest.mark.parametrize("plane,coef_key", [((0, 1), "spatial"), ((0, 3), "temporal")])
+def test_anisotropic_clover_abelian_field(plane, coef_key):
+    """Constant abelian field in one plane: A = 1 - kappa c sigma (x) F with c = c_SW^r/xi0
+    for a spatial plane and c_SW^t for a plane containing t."""
+    mu, nu = plane
+    dims = (8, 4, 2, 8)
+    lmu = dims[mu]
+    B = 2 * np.pi / lmu
+    U = L.gauge_from_qdp(W.unit_gauge(dims), dims)
+    coord = np.meshgrid(np.arange(dims[3]), np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]),
+                        indexing="ij")[3 - mu]
+    U[nu][..., 0, 0] = np.exp(1j * B * coord)
+    U[nu][..., 1, 1] = np.exp(1j * B * coord)
+    U[nu][..., 2, 2] = np.exp(-2j * B * coord)
+    d = np.array([np.sin(B), np.sin(B), -np.sin(2 * B)])
+    F = 1j * np.diag(d - d.sum() / 3)
+    kappa = 0.1
+    op = dirac.anisotropic(U, kappa, **ANISO)
+    c = ANISO["csw_r"] / ANISO["xi0"] if coef_key == "spatial" else ANISO["csw_t"]
+    expect = np.eye(12) - kappa * c * np.kron(sigma(mu, nu), F)
+    np.testing.assert_allclose(op.A, np.broadcast_to(expect, op.A.shape), atol=1e-14)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 4)])
+def test_anisotropic_dense_matrix_and_gamma5(dims):
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.7, 33), dims)
+    kappa = 0.1
+    op = dirac.anisotropic(U, kappa, **ANISO)
+    M = dense_matrix(U, dims, kappa, 0.0, -1, aniso=(ANISO["xi0"], ANISO["nu"], ANISO["csw_t"], ANISO["csw_r"]))
+    psi, phi = _rand_fermion(dims, 34), _rand_fermion(dims, 35)
+    np.testing.assert_allclose(op.M(psi).ravel(), M @ psi.ravel(), atol=1e-13)
+    lhs = np.vdot(phi, op.M(psi))
+    assert abs(lhs - np.vdot(dirac.gamma5(op.M(dirac.gamma5(phi))), psi)) < 1e-12 * abs(lhs)
