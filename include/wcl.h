@@ -141,6 +141,17 @@ wcl_status wcl_create(wcl_ctx** out, const int dims[4], int t_boundary, int devi
  * 6x6 block in FP64 and stored in every precision. */
 wcl_status wcl_load_gauge(wcl_ctx* ctx, const void* d_gauge, double kappa, double csw);
 
+/* Anisotropic form of Eq. 5 (Sec. III.B):
+ *   2 kappa a_t M = 1 - kappa [ W_4 + (nu/xi0) sum_i W_i
+ *                               + c_sw^t sum_i sigma_i4 F_i4 + (c_sw^r/xi0) sum_{i<j} sigma_ij F_ij ]
+ * (W_mu the Wilson hops of the isotropic operator above).  Everything else is as for
+ * wcl_load_gauge; wcl_load_gauge(kappa, csw) is the case xi0 = nu = 1,
+ * c_sw^t = c_sw^r = csw.  Internally the hopping parameter is kappa nu/xi0 with the
+ * t hops weighted by xi0/nu, so solutions and residuals are those of the operator
+ * above.  WCL_ERR_INVALID_ARG unless all values are finite and xi0, nu > 0. */
+wcl_status wcl_load_gauge_aniso(wcl_ctx* ctx, const void* d_gauge, double kappa, double xi0, double nu,
+                                double csw_t, double csw_r);
+
 /* Fermion buffers (d_in, d_out, d_x, d_b below) are device memory of the
  * context's GPU, or page-locked host memory (cudaHostAlloc / cudaHostRegister),
  * which the import and export kernels read and write in place through its device
@@ -247,6 +258,10 @@ wcl_status wcl_gamma(int n, double* h_out);
 /* kappa = 1 / (2 (m0 + 4)): the relation under Eq. 5 with xi_0 = nu = 1 (isotropic).
  * Host only; WCL_ERR_INVALID_ARG unless m0 is finite and m0 > -4. */
 wcl_status wcl_kappa_from_mass(double m0, double* kappa);
+
+/* kappa = 1 / (2 (m0 + 1 + 3 nu/xi0)), the relation under Eq. 5.  Host only;
+ * WCL_ERR_INVALID_ARG unless the values are finite, xi0, nu > 0 and the bracket > 0. */
+wcl_status wcl_kappa_from_mass_aniso(double m0, double xi0, double nu, double* kappa);
 
 /* The twelve spin-colour wall sources on timeslice t0 (Sec. III.B): d_b12 is
  * [12][fermion]; fermion k = 3 s + c is exp(+i p.x) (1 at zero momentum) in spin s,

@@ -15,6 +15,7 @@ from .wcl import (  # noqa: F401
     wcl_gamma,
     wcl_invert_batch,
     wcl_kappa_from_mass,
+    wcl_kappa_from_mass_aniso,
     wcl_status_string,
 )
 

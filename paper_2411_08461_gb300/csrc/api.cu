@@ -1,5 +1,6 @@
 // The C ABI of libwcl (declarations and documentation in include/wcl.h).
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -211,15 +212,11 @@ wcl_status wcl_create(wcl_ctx** out, const int dims[4], int t_boundary, int devi
   return WCL_OK;
 }
 
-wcl_status wcl_load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, double csw) {
-  if (!c || !d_gauge) {
-    set_error("wcl_load_gauge: null pointer");
-    return WCL_ERR_INVALID_ARG;
-  }
-  if (!(kappa == kappa) || !(csw == csw)) {
-    set_error("wcl_load_gauge: kappa or csw is NaN");
-    return WCL_ERR_INVALID_ARG;
-  }
+// shared by the isotropic and anisotropic loaders: the operator is
+// M = A - kappa H with the t hops of H weighted by tw and A built with csw_t on the
+// planes that contain t and csw_s on the spatial planes
+static wcl_status load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, double tw, double csw_t, double csw_s,
+                             const char* name) {
   WCL_CHECK(enter(c));
   if (!c->lat.gauge[0][0]) {
     wcl_status s = alloc_lattice(c);
@@ -230,29 +227,59 @@ wcl_status wcl_load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, double 
   }
   c->lat.loaded = false;
   c->lat.kappa = kappa;
-  c->lat.csw = csw;
+  c->lat.csw = csw_s;
+  c->lat.tw = tw;
   WCL_CUDA(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
   WCL_CUDA(import_gauge(c->lat, d_gauge, c->d_flags, c->stream));
   count_launch(c);
-  WCL_CUDA(build_clover(c->lat, d_gauge, kappa, csw, c->d_flags, c->stream));
+  WCL_CUDA(build_clover(c->lat, d_gauge, kappa, csw_t, csw_s, c->d_flags, c->stream));
   count_launch(c, false);
   WCL_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   WCL_CHECK(leave(c, WCL_OK));
   const int f = c->h_flags[0];
   if (f & 1) {
-    set_error("wcl_load_gauge: non-finite link entries");
+    set_error("%s: non-finite link entries", name);
     return WCL_ERR_NONFINITE;
   }
   if (f & 2) {
-    set_error("wcl_load_gauge: a link deviates from SU(3) by more than 1e-12");
+    set_error("%s: a link deviates from SU(3) by more than 1e-12", name);
     return WCL_ERR_RECONSTRUCT;
   }
   if (f & 4) {
-    set_error("wcl_load_gauge: singular clover block");
+    set_error("%s: singular clover block", name);
     return WCL_ERR_INVALID_ARG;
   }
   c->lat.loaded = true;
   return WCL_OK;
+}
+
+wcl_status wcl_load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, double csw) {
+  if (!c || !d_gauge) {
+    set_error("wcl_load_gauge: null pointer");
+    return WCL_ERR_INVALID_ARG;
+  }
+  if (!(kappa == kappa) || !(csw == csw)) {
+    set_error("wcl_load_gauge: kappa or csw is NaN");
+    return WCL_ERR_INVALID_ARG;
+  }
+  return load_gauge(c, d_gauge, kappa, 1.0, csw, csw, "wcl_load_gauge");
+}
+
+wcl_status wcl_load_gauge_aniso(wcl_ctx* c, const void* d_gauge, double kappa, double xi0, double nu, double csw_t,
+                                double csw_r) {
+  if (!c || !d_gauge) {
+    set_error("wcl_load_gauge_aniso: null pointer");
+    return WCL_ERR_INVALID_ARG;
+  }
+  if (!std::isfinite(kappa) || !std::isfinite(csw_t) || !std::isfinite(csw_r) || !std::isfinite(xi0) ||
+      !std::isfinite(nu) || !(xi0 > 0) || !(nu > 0)) {
+    set_error("wcl_load_gauge_aniso: kappa, c_sw^t, c_sw^r must be finite and xi0, nu positive");
+    return WCL_ERR_INVALID_ARG;
+  }
+  // kappa [W_4 + (nu/xi0) sum_i W_i] = (kappa nu/xi0) [(xi0/nu) W_4 + sum_i W_i]; the clover
+  // coefficients are rescaled by the same factor so that kappa' c' equals kappa c
+  const double kl = kappa * nu / xi0, tw = xi0 / nu;
+  return load_gauge(c, d_gauge, kl, tw, csw_t * tw, csw_r / nu, "wcl_load_gauge_aniso");
 }
 
 wcl_status wcl_apply_D(wcl_ctx* c, void* d_out, const void* d_in, wcl_prec prec, int nrhs) {

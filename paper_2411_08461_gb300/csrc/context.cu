@@ -79,6 +79,9 @@ Batch make_batch(const std::vector<wcl_ctx*>& ctxs, int nrhs, int block, int cap
     g.block_begin = blocks;
     g.slot_base = l * nrhs;
     g.tb = (float)L.tb;
+    g.tw = L.tw;
+    g.tw_f = (float)L.tw;
+    g.tbw_f = (float)((double)L.tb * L.tw);
     blocks += g.nchunk * nrhs;
   }
   b.total_blocks = blocks;

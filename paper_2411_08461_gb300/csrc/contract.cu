@@ -384,6 +384,17 @@ wcl_status wcl_kappa_from_mass(double m0, double* kappa) {
   return WCL_OK;
 }
 
+wcl_status wcl_kappa_from_mass_aniso(double m0, double xi0, double nu, double* kappa) {
+  const double d = m0 + 1.0 + 3.0 * nu / xi0;
+  if (!kappa || !std::isfinite(m0) || !std::isfinite(xi0) || !std::isfinite(nu) || !(xi0 > 0) || !(nu > 0) ||
+      !(d > 0)) {
+    set_error("wcl_kappa_from_mass_aniso: need finite m0, positive xi0 and nu, and m0 + 1 + 3 nu/xi0 > 0");
+    return WCL_ERR_INVALID_ARG;
+  }
+  *kappa = 1.0 / (2.0 * d);
+  return WCL_OK;
+}
+
 wcl_status wcl_wall_source(wcl_ctx* c, void* d_b12, int t0, const int* mom) {
   if (!c || !d_b12 || t0 < 0 || t0 >= c->lat.dims[3]) {
     set_error("wcl_wall_source: invalid argument (t0 must be 0..Lt-1)");

@@ -255,7 +255,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& a, const Slice& s,
                         (z == 0) ? i + (long)(Lz - 1) * plane : i - plane,
                         (t == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3};
     hop_all_compact<P, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb,
-                            (t + 1 == Lt) ? R(g.tb) : R(1), (t == 0) ? R(g.tb) : R(1));
+                            hop_t_weight<R>(g, t + 1 == Lt), hop_t_weight<R>(g, t == 0));
   } else {
   {
     const long jf = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
@@ -275,8 +275,8 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& a, const Slice& s,
   {
     const long jf = (t + 1 == Lt) ? i - (long)(Lt - 1) * vol3 : i + vol3;
     const long jb = (t == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3;
-    const R sf = (t + 1 == Lt) ? R(g.tb) : R(1);
-    const R sb = (t == 0) ? R(g.tb) : R(1);
+    const R sf = hop_t_weight<R>(g, t + 1 == Lt);
+    const R sb = hop_t_weight<R>(g, t == 0);
     hop_dir<P, 3, DAG>(acc, in, in_norm, g_here, g_there, stride, i, jf, jb, sf, sb);
   }
   }
@@ -815,8 +815,8 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
     const int tb = Tb[ls];
-    const R sf = (tb & 1) ? R(g.tb) : R(1);
-    const R sb = (tb & 2) ? R(g.tb) : R(1);
+    const R sf = hop_t_weight<R>(g, tb & 1);
+    const R sb = hop_t_weight<R>(g, tb & 2);
     if constexpr (ASYNC) {
       extern __shared__ uint4 stage_mem[];
       const int nt = blockDim.x;

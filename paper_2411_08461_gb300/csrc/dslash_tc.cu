@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(TC_WARPS * 32) dslash_tc_kernel(const __grid_c
     jn[5] = (z == 0) ? i + (long)(Lz - 1) * plane : i - plane;
     jn[6] = (tt + 1 == Lt) ? i - (long)(Lt - 1) * vol3 : i + vol3;
     jn[7] = (tt == 0) ? i + (long)(Lt - 1) * vol3 : i - vol3;
-    const float eta_f = (tt + 1 == Lt) ? G.tb : 1.f, eta_b = (tt == 0) ? G.tb : 1.f;
+    const float eta_f = (tt + 1 == Lt) ? G.tbw_f : G.tw_f, eta_b = (tt == 0) ? G.tbw_f : G.tw_f;
 
     // ---- stage norms and the row scale (largest neighbour norm of each rhs) ----
     float nrm[4];

@@ -213,7 +213,9 @@ __device__ void pack_block(double2* dst, long st, long i, int b, const cpx<doubl
     for (int c = 0; c < r; c++, k++) dst[(18 * b + 3 + k) * st + i] = make_double2(m[r][c].re, m[r][c].im);
 }
 
-__global__ void clover_build_kernel(const double2* __restrict__ qdp, QdpGeom q, double kappa, double csw,
+// csw_t multiplies the planes (mu, 3) that contain t, csw_s the spatial planes
+__global__ void clover_build_kernel(const double2* __restrict__ qdp, QdpGeom q, double kappa, double csw_t,
+                                    double csw_s,
                                     double2* A0, double2* A1, double2* Ai0, double2* Ai1, long st,
                                     int* __restrict__ flags) {
   const long n = 2 * q.vh;
@@ -247,7 +249,7 @@ __global__ void clover_build_kernel(const double2* __restrict__ qdp, QdpGeom q, 
         for (int b = 0; b < 2; b++)
           for (int s1 = 0; s1 < 2; s1++)
             for (int s2 = 0; s2 < 2; s2++) {
-              const cpx<double> sv = (-kappa * csw) * sg[2 * b + s1][2 * b + s2];
+              const cpx<double> sv = (-kappa * (nu == 3 ? csw_t : csw_s)) * sg[2 * b + s1][2 * b + s2];
               for (int ca = 0; ca < 3; ca++)
                 for (int cb = 0; cb < 3; cb++) blk[b][3 * s1 + ca][3 * s2 + cb] = blk[b][3 * s1 + ca][3 * s2 + cb] + sv * F.m[ca][cb];
             }
@@ -418,10 +420,10 @@ cudaError_t import_gauge(const LatticeDevice& L, const void* d_qdp, int* d_flags
   return e;
 }
 
-cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw, int* d_flags,
-                         cudaStream_t st) {
+cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw_t, double csw_s,
+                         int* d_flags, cudaStream_t st) {
   clover_build_kernel<<<grid_for(2 * L.vh, 64), 64, 0, st>>>(
-      static_cast<const double2*>(d_qdp), qgeom(L), kappa, csw, static_cast<double2*>(L.clov[F64][0]),
+      static_cast<const double2*>(d_qdp), qgeom(L), kappa, csw_t, csw_s, static_cast<double2*>(L.clov[F64][0]),
       static_cast<double2*>(L.clov[F64][1]), static_cast<double2*>(L.clovinv[F64][0]),
       static_cast<double2*>(L.clovinv[F64][1]), L.stride, d_flags);
   cudaError_t e = cudaGetLastError();

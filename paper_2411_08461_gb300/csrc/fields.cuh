@@ -10,6 +10,7 @@ struct LatticeDevice {
   long vh = 0;          // sites per parity
   long stride = 0;      // padded sites per chunk
   double kappa = 0, csw = 0;
+  double tw = 1.0;      // t-hop weight: xi_0 / nu of the anisotropic operator (kappa holds kappa nu / xi_0)
   bool loaded = false;
   // [prec][parity], prec = F64, F32, F16, BF16, DF64 (the FP64 values split into float pairs)
   void* gauge[5][2] = {};    // links, [mu][chunk][stride]; 18 reals (FP64, DF64) or 12 (row 2 rebuilt)
@@ -50,7 +51,8 @@ cudaError_t propagator_layout(const LatticeDevice& L, const void* src, void* dst
 
 // d_flags bits: 1 non-finite input, 2 link not SU(3), 4 singular clover block
 cudaError_t import_gauge(const LatticeDevice& L, const void* d_qdp, int* d_flags, cudaStream_t st);
-cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw, int* d_flags,
+cudaError_t build_clover(const LatticeDevice& L, const void* d_qdp, double kappa, double csw_t, double csw_s,
+                         int* d_flags,
                          cudaStream_t st);
 // complex-element strides: rhs_stride_c between right-hand sides, par_off_c to the parity block
 cudaError_t import_fermion(const LatticeDevice& L, const void* d_src, long rhs_stride_c, long par_off_c, int nrhs,

@@ -24,6 +24,7 @@
 //     36 reals per block, 72 per site.
 //     F64 : 36 double2, F32 : 18 float4, F16/BF16 : 9 uint4 + float norm[i].
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -626,7 +627,22 @@ struct LatGeom {
   int slot_base;    // index of (lattice, rhs = 0) in per-slice arrays
   float tb;         // fermion time boundary sign
   int zblk;         // multi-RHS kernel: z planes per block of its tile order (0: tiles in site order)
+  double tw;        // weight of the t hops relative to the spatial ones (xi_0 / nu; 1 isotropic)
+  float tw_f;       // tw and tb * tw rounded to FP32 for the FP32 / 16-bit kernels
+  float tbw_f;
 };
+
+// factor of a t hop: tw inside the lattice, tb * tw across the time boundary
+template <typename R>
+__device__ __forceinline__ R hop_t_weight(const LatGeom& g, bool edge) {
+  if constexpr (std::is_same<R, double>::value) {
+    return edge ? (double)g.tb * g.tw : g.tw;
+  } else if constexpr (std::is_same<R, float>::value) {
+    return edge ? g.tbw_f : g.tw_f;
+  } else {
+    return R(edge ? (double)g.tb * g.tw : g.tw);  // double-float: split once per thread
+  }
+}
 
 struct Batch {
   int nlat;

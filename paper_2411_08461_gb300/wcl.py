@@ -75,6 +75,10 @@ SIGNATURES = {
     "wcl_last_error": (ctypes.c_char_p, []),
     "wcl_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, _P]),
     "wcl_load_gauge": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double]),
+    "wcl_load_gauge_aniso": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double]),
+    "wcl_kappa_from_mass_aniso": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.POINTER(ctypes.c_double)]),
     "wcl_apply_D": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "wcl_apply_Mpc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "wcl_fermions_to_propagator": (ctypes.c_int, [_P, _P, _P]),
@@ -178,6 +182,13 @@ def wcl_kappa_from_mass(m0: float) -> float:
     return k.value
 
 
+def wcl_kappa_from_mass_aniso(m0: float, xi0: float, nu: float) -> float:
+    k = ctypes.c_double()
+    _check(load_library().wcl_kappa_from_mass_aniso(float(m0), float(xi0), float(nu), ctypes.byref(k)),
+           "wcl_kappa_from_mass_aniso")
+    return k.value
+
+
 def _mom_arg(mom):
     if mom is None:
         return None
@@ -228,6 +239,13 @@ class Context:
 
         _check(load_library().wcl_load_gauge(self.handle, _ptr(gauge, torch.complex128, self.volume * 36, "gauge"),
                                              float(kappa), float(csw)), "wcl_load_gauge")
+
+    def wcl_load_gauge_aniso(self, gauge, kappa: float, xi0: float, nu: float, csw_t: float, csw_r: float):
+        import torch
+
+        _check(load_library().wcl_load_gauge_aniso(self.handle, _ptr(gauge, torch.complex128, self.volume * 36, "gauge"),
+                                                   float(kappa), float(xi0), float(nu), float(csw_t), float(csw_r)),
+               "wcl_load_gauge_aniso")
 
     def wcl_apply_D(self, out, inp, prec: str = "f64", nrhs: int = 1):
         import torch
