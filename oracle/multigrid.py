@@ -1,0 +1,186 @@
+"""Adaptive aggregation multigrid preconditioner for the Wilson-clover operator, the
+solver the paper enables by passing a block size per level (Sec. II.E: the multigrid
+parameters follow QUDA's test example with the geometric block size left open; Sec.
+III.B: two levels, each projecting a 2^4 sublattice onto one coarse site).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  The paper names the method
+without its steps; the reading taken here is the standard aggregation-based one:
+
+* null space: N_v vectors from random starts (passed in) relaxed towards the
+  near-kernel of the operator by minimal-residual steps on A x = 0;
+* prolongator P: per block of sites and per chirality (gamma_5 = diag(1, 1, -1, -1)
+  on the fine level, the first coarse index on coarser ones), the restrictions of the
+  null vectors orthonormalised (QR): P^+ P = 1, and P commutes with gamma_5;
+* coarse operator A_c = P^+ A P (Galerkin), applied as that product;
+* preconditioner (one cycle): minimal-residual pre-smoothing from zero, coarse
+  correction P A_c^-1 P^+ r with the coarse system solved by flexible GCR to a
+  relative tolerance (recursively preconditioned by the next level: a K-cycle), then
+  minimal-residual post-smoothing;
+* outer solver: flexible GCR (oracle.solvers.fgcr) with this preconditioner.
+
+Vectors of a level are arrays with the four site axes (Lt, Lz, Ly, Lx) first and the
+level's internal axes after: (4, 3) spin-colour on the fine level, (2, N_v) chirality
+and vector index on a coarse one.
+
+Pins (tests/test_oracle_multigrid.py): orthonormality and chirality of P, the
+gamma_5-hermiticity the coarse operator inherits, exactness when the null space
+spans each block, and the iteration reduction against plain GCR.
+"""
+import numpy as np
+
+from . import solvers
+
+
+def chirality_halves(internal_shape):
+    """Index tuples into the internal axes selecting chirality +1 and -1."""
+    if internal_shape == (4, 3):
+        return (np.s_[0:2, :], np.s_[2:4, :])
+    return (np.s_[0:1, :], np.s_[1:2, :])
+
+
+def _blocked(v, block):
+    """(Lt, Lz, Ly, Lx, ...) -> (Ct, Cz, Cy, Cx, bt, bz, by, bx, ...) with block = (bx, by, bz, bt)."""
+    lt, lz, ly, lx = v.shape[:4]
+    bx, by, bz, bt = block
+    tail = v.shape[4:]
+    w = v.reshape((lt // bt, bt, lz // bz, bz, ly // by, by, lx // bx, bx) + tail)
+    return w.transpose((0, 2, 4, 6, 1, 3, 5, 7) + tuple(range(8, 8 + len(tail))))
+
+
+def _unblocked(w, block):
+    ct, cz, cy, cx, bt, bz, by, bx = w.shape[:8]
+    tail = w.shape[8:]
+    v = w.transpose((0, 4, 1, 5, 2, 6, 3, 7) + tuple(range(8, 8 + len(tail))))
+    return v.reshape((ct * bt, cz * bz, cy * by, cx * bx) + tail)
+
+
+class Prolongator:
+    """P for one level: per coarse site and chirality an orthonormal basis (dof x N_v) of
+    the block-chirality restrictions of the null vectors."""
+
+    def __init__(self, vectors, block):
+        self.block = tuple(block)
+        self.nv = len(vectors)
+        self.internal = vectors[0].shape[4:]
+        self.halves = chirality_halves(self.internal)
+        fine_sites = vectors[0].shape[:4]
+        lt, lz, ly, lx = fine_sites
+        bx, by, bz, bt = self.block
+        if lx % bx or ly % by or lz % bz or lt % bt:
+            raise ValueError("block size must divide the lattice")
+        self.coarse_sites = (lt // bt, lz // bz, ly // by, lx // bx)
+        self.fine_shape = vectors[0].shape
+        self.basis = []  # per chirality: (Ct, Cz, Cy, Cx, dof, N_v)
+        for h in self.halves:
+            cols = []
+            for v in vectors:
+                w = _blocked(v, self.block)
+                part = w[(Ellipsis,) + h]  # (..., block sites..., half internal)
+                cols.append(part.reshape(self.coarse_sites + (-1,)))
+            m = np.stack(cols, axis=-1)  # (C..., dof, N_v)
+            if m.shape[-2] < self.nv:
+                raise ValueError("more null vectors than block-chirality degrees of freedom")
+            q, _ = np.linalg.qr(m)
+            self.basis.append(q)
+        self.coarse_shape = self.coarse_sites + (2, self.nv)
+
+    def restrict(self, v):
+        """P^+ v: fine vector -> coarse vector (Ct, Cz, Cy, Cx, 2, N_v)."""
+        w = _blocked(v, self.block)
+        out = np.zeros(self.coarse_shape, dtype=np.complex128)
+        for chi, h in enumerate(self.halves):
+            part = w[(Ellipsis,) + h].reshape(self.coarse_sites + (-1,))
+            out[..., chi, :] = np.einsum("...dn,...d->...n", np.conj(self.basis[chi]), part)
+        return out
+
+    def prolong(self, c):
+        """P c: coarse vector -> fine vector."""
+        w = np.zeros(_blocked(np.zeros(self.fine_shape, dtype=np.complex128), self.block).shape,
+                     dtype=np.complex128)
+        for chi, h in enumerate(self.halves):
+            part = np.einsum("...dn,...n->...d", self.basis[chi], c[..., chi, :])
+            w[(Ellipsis,) + h] = part.reshape(w[(Ellipsis,) + h].shape)
+        return _unblocked(w, self.block)
+
+
+def minres_relax(A, b, steps, x0=None):
+    """`steps` minimal-residual steps on A x = b: r = b - A x, alpha = <A r, r>/<A r, A r>,
+    x += alpha r.  With b = 0 this damps every component except the near-kernel."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A(x) if x0 is not None else b.copy()
+    for _ in range(steps):
+        ar = A(r)
+        den = solvers.norm2(ar)
+        if den == 0.0:
+            break
+        alpha = solvers.dot(ar, r) / den
+        x = x + alpha * r
+        r = r - alpha * ar
+    return x
+
+
+def null_vectors(A, starts, steps):
+    """Relax each random start towards A x = 0 and normalise it."""
+    out = []
+    zero = np.zeros_like(starts[0])
+    for s in starts:
+        v = minres_relax(A, zero, steps, x0=s)
+        out.append(v / np.sqrt(solvers.norm2(v)))
+    return out
+
+
+class Level:
+    """One level of the hierarchy: its operator, prolongator to the next coarser level,
+    the coarse operator P^+ A P and (recursively) the next level."""
+
+    def __init__(self, A, P, coarse=None, pre=2, post=2, coarse_tol=0.1, coarse_maxiter=50, coarse_nkrylov=8):
+        self.A, self.P, self.coarse = A, P, coarse
+        self.pre, self.post = pre, post
+        self.coarse_tol, self.coarse_maxiter, self.coarse_nkrylov = coarse_tol, coarse_maxiter, coarse_nkrylov
+        self.stats = {"coarse_iters": 0, "cycles": 0}
+
+    def Ac(self, c):
+        """Galerkin coarse operator P^+ A P."""
+        return self.P.restrict(self.A(self.P.prolong(c)))
+
+    def cycle(self, r):
+        """One preconditioner application e ~ A^-1 r."""
+        self.stats["cycles"] += 1
+        e = minres_relax(self.A, r, self.pre)
+        r1 = r - self.A(e)
+        rc = self.P.restrict(r1)
+        pc = self.coarse.cycle if self.coarse is not None else None
+        ec, info = solvers.fgcr(self.Ac, rc, precond=pc, tol=self.coarse_tol, maxiter=self.coarse_maxiter,
+                                nkrylov=self.coarse_nkrylov)
+        self.stats["coarse_iters"] += info["iters"]
+        e = e + self.P.prolong(ec)
+        if self.post:
+            e = minres_relax(self.A, r, self.post, x0=e)
+        return e
+
+
+def setup(A, fine_shape, blocks, nvs, starts_per_level, relax_steps=20, **level_kw):
+    """Build the hierarchy.  blocks: block size per level (fine first); nvs: N_v per
+    level; starts_per_level: for each level, N_v random starts shaped like that level's
+    vectors (random numbers are inputs, drawn by the caller)."""
+    ops = [A]
+    prolongators = []
+    shape = fine_shape
+    for lvl, (block, nv) in enumerate(zip(blocks, nvs)):
+        starts = starts_per_level[lvl]
+        assert len(starts) == nv and starts[0].shape == shape
+        vecs = null_vectors(ops[-1], starts, relax_steps)
+        P = Prolongator(vecs, block)
+        prolongators.append(P)
+        Aprev = ops[-1]
+        ops.append(lambda c, P=P, Aprev=Aprev: P.restrict(Aprev(P.prolong(c))))
+        shape = P.coarse_shape
+    level = None
+    for lvl in reversed(range(len(blocks))):
+        level = Level(ops[lvl], prolongators[lvl], coarse=level, **level_kw)
+    return level
+
+
+def solve(A, b, top, tol=1e-10, maxiter=500, nkrylov=20):
+    """Flexible GCR on A x = b preconditioned by one multigrid cycle per iteration."""
+    return solvers.fgcr(A, b, precond=top.cycle, tol=tol, maxiter=maxiter, nkrylov=nkrylov)

@@ -184,3 +184,10 @@ def gaussian_propagator_runs(dims, t: int, seed: int) -> np.ndarray:
     lx, ly, lz, lt = _check_dims(dims)
     z = np.random.default_rng([seed, t]).standard_normal((2, lz, ly, lx // 2, 4, 4, 3, 3, 2))
     return z[..., 0] + 1j * z[..., 1]
+
+
+def gaussian_complex(shape, seed: int) -> np.ndarray:
+    """Complex Gaussian array of any shape (re, im ~ N(0,1)), e.g. the random starts of a
+    coarse level's null-space vectors."""
+    z = np.random.default_rng(seed).standard_normal(tuple(shape) + (2,))
+    return z[..., 0] + 1j * z[..., 1]
