@@ -76,3 +76,33 @@ def test_gamma_and_kappa_helpers_without_a_gpu():
             wcl.wcl_kappa_from_mass(bad)
     with pytest.raises(wcl.WclError):
         wcl.wcl_gamma(16)
+
+
+def test_binding_argument_checks_without_a_gpu():
+    """The binding's marshalling rejects what the ABI cannot take before any call:
+    non-tensors, CPU tensors that are not page-locked, wrong dtype or size, non-contiguous
+    views, malformed Gamma matrices and momentum triples."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2411_08461_gb300 import wcl
+
+    with pytest.raises(TypeError):
+        wcl._ptr(np.zeros(4), name="x")
+    with pytest.raises(ValueError, match="CUDA device"):
+        wcl._ptr(torch.zeros(4, dtype=torch.complex128), name="x")
+    with pytest.raises(ValueError, match="pinned"):
+        wcl._ptr(torch.zeros(4, dtype=torch.complex128), name="x", fermion=True)
+    with pytest.raises(ValueError):
+        wcl._gamma_arg(np.eye(3))
+    buf, ptr = wcl._gamma_arg(1j * np.eye(4))
+    assert buf.shape == (32,) and buf[1] == 1.0 and buf[0] == 0.0  # row-major (re, im) pairs
+    assert wcl._gamma_arg(None) == (None, None)
+    with pytest.raises(ValueError):
+        wcl._mom_arg((1, 2))
+    m = wcl._mom_arg((0, -1, 3))
+    assert list(m) == [0, -1, 3]
+    assert wcl._mom_arg(None) is None
