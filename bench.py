@@ -206,10 +206,18 @@ def cpu_baseline_sample(gpu_iters_per_rhs: float, budget_s: float = 20.0):
     scale = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) / (dims[0] * dims[1] * dims[2] * dims[3])
     est = per_iter * scale * gpu_iters_per_rhs * 12
     cores = 1  # numpy elementwise and einsum kernels run on one thread
+    try:
+        affinity = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        affinity = None
+    threads = ", ".join(f"{k}={os.environ.get(k, 'unset')}" for k in
+                        ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"))
     return {"value": 1.0 / est, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} BiCGStab iterations of the FP64 oracle on 16^3x32 (same links/kappa/c_sw), "
                       f"{per_iter:.2f} s/iteration, scaled x{scale:.0f} by volume, x{gpu_iters_per_rhs:.0f} "
-                      f"iterations/RHS (the GPU solve's count) and x12 RHS; host has {os.cpu_count()} cores"}
+                      f"iterations/RHS (the GPU solve's count) and x12 RHS; host has {os.cpu_count()} cores, "
+                      f"{affinity} in this process's affinity mask, {threads}; numpy's elementwise "
+                      f"kernels are single-threaded"}
 
 
 def run_reference(args, rank, world):
