@@ -106,3 +106,41 @@ def test_binding_argument_checks_without_a_gpu():
     m = wcl._mom_arg((0, -1, 3))
     assert list(m) == [0, -1, 3]
     assert wcl._mom_arg(None) is None
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """include/wcl.h is a C header (C99, -pedantic) and a C program links against
+    libwcl.so and calls its host-only functions."""
+    import shutil
+    import subprocess
+
+    import __graft_entry__
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    __graft_entry__.build()
+    from paper_2411_08461_gb300 import wcl
+
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c",
+                    os.path.join(inc, "wcl.h")], check=True)
+    src = tmp_path / "user.c"
+    src.write_text(
+        '#include "wcl.h"\n'
+        "#include <stdio.h>\n"
+        "int main(void) {\n"
+        "  wcl_solve_params p; double g[32]; double k = 0;\n"
+        "  wcl_default_params(&p);\n"
+        "  if (wcl_gamma(15, g) != WCL_OK || g[0] != 1.0 || g[2 * 15] != -1.0) return 1;\n"
+        "  if (wcl_kappa_from_mass(0.0, &k) != WCL_OK || k != 0.125) return 2;\n"
+        "  if (wcl_kappa_from_mass_aniso(0.0, 2.0, 1.0, &k) != WCL_OK || k != 0.2) return 3;\n"
+        "  printf(\"%s\\n\", wcl_status_string(WCL_ERR_NOT_CONVERGED));\n"
+        "  return p.solver == WCL_BICGSTAB ? 0 : 4;\n"
+        "}\n")
+    libdir = os.path.dirname(wcl.LIB_PATH)
+    exe = tmp_path / "user"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-L", libdir, "-lwcl",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out
+    assert out.stdout.strip() == "not converged"
