@@ -1,0 +1,121 @@
+"""The oracle's pins catch plausible mistakes: each test plants one mistake in the
+oracle (on the CPU, through monkeypatch) and checks that the pin meant to guard that
+part now fails.  A pin that still passed would not be pinning anything."""
+import numpy as np
+import pytest
+
+import test_oracle_contract as TC
+import test_oracle_dirac as TD
+import test_oracle_multigrid as TM
+import test_oracle_ptc as TP
+import test_oracle_solvers as TS
+from oracle import contract, dirac, multigrid, ptc, solvers
+from oracle import lattice as L
+
+
+def _fails(fn, *args, **kw):
+    with pytest.raises(AssertionError):
+        fn(*args, **kw)
+
+
+def test_swapped_hopping_projectors(monkeypatch):
+    """(1 + gamma) forward and (1 - gamma) backward instead of the reverse."""
+    monkeypatch.setattr(dirac, "GAMMA", -dirac.GAMMA)
+    _fails(TD.test_free_field_plane_wave, (1, 0, 2, 1), -1)
+    _fails(TD.test_dense_matrix_matches, (2, 2, 2, 2), -1)
+
+
+def test_dropped_antiperiodic_sign(monkeypatch):
+    monkeypatch.setattr(L, "time_boundary_sign", lambda dims, tb, fwd: np.ones(dims[::-1]))
+    _fails(TD.test_free_field_plane_wave, (1, 0, 2, 1), -1)
+
+
+def test_clover_sign(monkeypatch):
+    orig = dirac.sigma
+    monkeypatch.setattr(dirac, "sigma", lambda mu, nu: -orig(mu, nu))
+    _fails(TD.test_clover_abelian_constant_field, 1)
+
+
+def test_transposed_field_strength(monkeypatch):
+    orig = dirac.field_strength
+    monkeypatch.setattr(dirac, "field_strength", lambda U, mu, nu: np.swapaxes(orig(U, mu, nu), -1, -2))
+    _fails(TD.test_dense_matrix_matches, (4, 2, 2, 4), -1)
+
+
+def test_missing_trace_subtraction(monkeypatch):
+    def no_trace(U, mu, nu):
+        q = dirac.clover_leaves(U, mu, nu)
+        return (q - dirac._dag(q)) / 8.0
+
+    monkeypatch.setattr(dirac, "field_strength", no_trace)
+    _fails(TD.test_clover_abelian_constant_field, 1)
+
+
+def test_wrong_schur_source_sign(monkeypatch):
+    def bad(self, b):
+        t = dirac.apply_site_matrix(self.Ainv, b * self.odd)
+        return (b - self.kappa * self.H(t)) * self.even
+
+    monkeypatch.setattr(dirac.WilsonClover, "schur_source", bad)
+    _fails(TD.test_dense_matrix_matches, (2, 2, 2, 2), -1)
+
+
+def test_wrong_reconstruction_sign(monkeypatch):
+    """x_o = A_oo^-1 (b_o - kappa D_oe x_e) instead of + kappa."""
+    def bad(self, xe, b):
+        xe = xe * self.even
+        xo = dirac.apply_site_matrix(self.Ainv, (b - self.kappa * self.H(xe)) * self.odd) * self.odd
+        return xe + xo
+
+    monkeypatch.setattr(dirac.WilsonClover, "reconstruct", bad)
+    _fails(TS.test_even_odd_solve_matches_dense, (2, 2, 2, 2), "bicgstab")
+
+
+def test_anisotropic_weight_on_the_wrong_axis(monkeypatch):
+    orig = dirac.anisotropic
+
+    def bad(U, kappa, xi0, nu, csw_t, csw_r, t_boundary=-1):
+        op = orig(U, kappa, xi0, nu, csw_t, csw_r, t_boundary)
+        w = nu / xi0
+        op.hop_weights = (1.0, w, w, w)  # t weighted, x not
+        return op
+
+    monkeypatch.setattr(dirac, "anisotropic", bad)
+    _fails(TD.test_anisotropic_free_field_plane_wave, (1, 0, 2, 1))
+
+
+def test_transposed_gamma_in_contraction(monkeypatch):
+    orig = contract.contract
+    monkeypatch.setattr(contract, "contract",
+                        lambda A, B, gamma=None, mom=(0, 0, 0): orig(A, B, None if gamma is None else gamma.T, mom))
+    _fails(TC.test_contract_gamma_structure)
+
+
+def test_momentum_phase_sign(monkeypatch):
+    orig = contract.momentum_phase
+    monkeypatch.setattr(contract, "momentum_phase", lambda dims, mom: np.conj(orig(dims, mom)))
+    import workloads as W
+    from _dense_ref import dense_matrix
+
+    U = L.gauge_from_qdp(W.gauge_links(TC.DIMS, 0.4, 5), TC.DIMS)
+    op = dirac.WilsonClover(U, TC.KAPPA, TC.CSW)
+    Minv = np.linalg.inv(dense_matrix(U, TC.DIMS, TC.KAPPA, TC.CSW))
+    _fails(TC.test_wall_source_two_point_eq1_third_line, (U, op, Minv))
+
+
+def test_multigrid_wrong_chirality_split(monkeypatch):
+    """Splitting spins (0, 2) / (1, 3) instead of the gamma_5 eigenspaces."""
+    orig = multigrid.chirality_halves
+
+    def bad(internal):
+        if internal == (4, 3):
+            return (np.s_[0:4:2, :], np.s_[1:4:2, :])
+        return orig(internal)
+
+    monkeypatch.setattr(multigrid, "chirality_halves", bad)
+    _fails(TM.test_coarse_operator_inherits_gamma5_hermiticity)
+
+
+def test_transport_without_dagger(monkeypatch):
+    monkeypatch.setattr(ptc, "_dag", lambda u: u)
+    _fails(TP.test_transport_adjoint)
