@@ -119,3 +119,56 @@ def test_multigrid_wrong_chirality_split(monkeypatch):
 def test_transport_without_dagger(monkeypatch):
     monkeypatch.setattr(ptc, "_dag", lambda u: u)
     _fails(TP.test_transport_adjoint)
+
+
+def test_network_gradient_without_conjugate(monkeypatch):
+    """The weight gradient of a layer built from T_s x instead of conj(T_s x)."""
+    def bad(U, W, x, g_out, t_boundary=-1):
+        cout, cin = W.shape[:2]
+        gW = np.zeros_like(W)
+        gx = np.zeros_like(x)
+        for c in range(cin):
+            for s in range(ptc.NSHIFT):
+                ts = ptc.transport(U, x[c], s, t_boundary)
+                go = g_out.reshape(cout, -1, 4, 3)
+                gW[:, c, s] = np.einsum("oxac,xbc->oab", go, ts.reshape(-1, 4, 3))
+                back = np.einsum("oba,o...bc->...ac", W[:, c, s].conj(), g_out)
+                gx[c] += ptc.transport_adjoint(U, back, s, t_boundary)
+        return gW, gx
+
+    monkeypatch.setattr(ptc, "layer_backward", bad)
+    _fails(TP.test_gradient_finite_differences, 0)
+
+
+def test_sequential_source_gamma_on_the_wrong_index(monkeypatch):
+    """gamma_5 applied to the source spin of S_0 instead of its sink spin."""
+    def bad(S, t, mom=(0, 0, 0), gamma=None):
+        gm = contract.G.GAMMA5 if gamma is None else gamma
+        dims = (S.shape[3], S.shape[2], S.shape[1], S.shape[0])
+        ph = np.conj(contract.momentum_phase(dims, mom))
+        X = np.zeros_like(S)
+        X[t] = np.einsum("...jkab,kl->...jlab", S[t], gm.T) * ph[t][..., None, None, None, None]
+        return X
+
+    monkeypatch.setattr(contract, "sequential_source", bad)
+    import workloads as W
+    from _dense_ref import dense_matrix
+
+    U = L.gauge_from_qdp(W.gauge_links(TC.DIMS, 0.4, 5), TC.DIMS)
+    op = dirac.WilsonClover(U, TC.KAPPA, TC.CSW)
+    Minv = np.linalg.inv(dense_matrix(U, TC.DIMS, TC.KAPPA, TC.CSW))
+    _fails(TC.test_three_point_eq3_eq4, (U, op, Minv))
+
+
+def test_restriction_without_conjugate(monkeypatch):
+    """P^T v instead of P^+ v."""
+    def bad(self, v):
+        w = multigrid._blocked(v, self.block)
+        out = np.zeros(self.coarse_shape, dtype=np.complex128)
+        for chi, h in enumerate(self.halves):
+            part = w[(Ellipsis,) + h].reshape(self.coarse_sites + (-1,))
+            out[..., chi, :] = np.einsum("...dn,...d->...n", self.basis[chi], part)
+        return out
+
+    monkeypatch.setattr(multigrid.Prolongator, "restrict", bad)
+    _fails(TM.test_prolongator_orthonormal_and_chiral)
