@@ -22,9 +22,14 @@ Vectors of a level are arrays with the four site axes (Lt, Lz, Ly, Lx) first and
 level's internal axes after: (4, 3) spin-colour on the fine level, (2, N_v) chirality
 and vector index on a coarse one.
 
+The coarse operator is also available as the nine-point stencil a GPU kernel would
+apply (coarse_stencil / apply_stencil), read off the Galerkin product column by
+column.
+
 Pins (tests/test_oracle_multigrid.py): orthonormality and chirality of P, the
-gamma_5-hermiticity the coarse operator inherits, exactness when the null space
-spans each block, and the iteration reduction against plain GCR.
+gamma_5-hermiticity the coarse operator and its stencil blocks inherit, the stencil
+against the Galerkin product, exactness when the null space spans each block, and
+the iteration reduction against plain GCR.
 """
 import numpy as np
 
@@ -184,3 +189,50 @@ def setup(A, fine_shape, blocks, nvs, starts_per_level, relax_steps=20, **level_
 def solve(A, b, top, tol=1e-10, maxiter=500, nkrylov=20):
     """Flexible GCR on A x = b preconditioned by one multigrid cycle per iteration."""
     return solvers.fgcr(A, b, precond=top.cycle, tol=tol, maxiter=maxiter, nkrylov=nkrylov)
+
+
+def coarse_stencil(A, P):
+    """The coarse operator P^+ A P of a nearest-neighbour fine operator as a nine-point
+    stencil on the coarse lattice: (A_c c)(x) = X(x) c(x) + sum_mu [Yf_mu(x) c(x + mu)
+    + Yb_mu(x) c(x - mu)], every block (2 N_v) x (2 N_v).  Read off column by column:
+    A_c applied to the unit coarse vector of site y and component j has X(y)[:, j] at y,
+    Yf_mu(y - mu)[:, j] at y - mu and Yb_mu(y + mu)[:, j] at y + mu.  Needs every coarse
+    extent >= 3 so that y + mu and y - mu are different sites.  Returns (X, Yf, Yb) with
+    X: (Ct, Cz, Cy, Cx, n, n), Yf, Yb: (4, Ct, Cz, Cy, Cx, n, n), n = 2 N_v."""
+    ct, cz, cy, cx = P.coarse_sites
+    if min(ct, cz, cy, cx) < 3:
+        raise ValueError("coarse extents must be at least 3")
+    nv = P.nv
+    n = 2 * nv
+    X = np.zeros(P.coarse_sites + (n, n), dtype=np.complex128)
+    Yf = np.zeros((4,) + X.shape, dtype=np.complex128)
+    Yb = np.zeros_like(Yf)
+    ext = (cx, cy, cz, ct)  # direction mu = 0..3 is x, y, z, t
+    for site in np.ndindex(*P.coarse_sites):  # (t, z, y, x)
+        for j in range(n):
+            e = np.zeros(P.coarse_shape, dtype=np.complex128)
+            e[site + (j // nv, j % nv)] = 1.0
+            col = P.restrict(A(P.prolong(e))).reshape(P.coarse_sites + (n,))
+            X[site][:, j] = col[site]
+            for mu in range(4):
+                ax = 3 - mu
+                dn = list(site)
+                dn[ax] = (dn[ax] - 1) % ext[mu]
+                up = list(site)
+                up[ax] = (up[ax] + 1) % ext[mu]
+                Yf[mu][tuple(dn)][:, j] = col[tuple(dn)]
+                Yb[mu][tuple(up)][:, j] = col[tuple(up)]
+    return X, Yf, Yb
+
+
+def apply_stencil(X, Yf, Yb, c):
+    """(A_c c)(x) from the nine-point stencil of coarse_stencil."""
+    shape = c.shape
+    sites = shape[:4]
+    v = c.reshape(sites + (-1,))
+    out = np.einsum("...ij,...j->...i", X, v)
+    for mu in range(4):
+        ax = 3 - mu
+        out += np.einsum("...ij,...j->...i", Yf[mu], np.roll(v, -1, axis=ax))
+        out += np.einsum("...ij,...j->...i", Yb[mu], np.roll(v, +1, axis=ax))
+    return out.reshape(shape)

@@ -92,3 +92,21 @@ def test_multigrid_cuts_iterations(levels):
     x, info = MG.solve(op.M, b, top, tol=tol)
     assert op.true_residual(x, b) <= tol * 1.01
     assert info["iters"] * 4 <= plain["iters"], (info["iters"], plain["iters"])
+
+
+def test_coarse_stencil_equals_galerkin_product():
+    """The nine-point coarse stencil read off column by column reproduces P^+ M P on
+    random coarse vectors, and its blocks inherit gamma_5-hermiticity:
+    Yb_mu(x + mu) = G5 Yf_mu(x)^+ G5 and X = G5 X^+ G5."""
+    dims, block, nv = (6, 6, 6, 6), (2, 2, 2, 2), 2
+    op = _op(dims, 0.12, seed=8)
+    top = MG.setup(op.M, (6, 6, 6, 6, 4, 3), [block], [nv], [_starts(dims, nv, 60)], relax_steps=3)
+    X, Yf, Yb = MG.coarse_stencil(op.M, top.P)
+    for seed in (1, 2):
+        c = W.gaussian_complex(top.P.coarse_shape, seed)
+        np.testing.assert_allclose(MG.apply_stencil(X, Yf, Yb, c), top.Ac(c), atol=1e-12)
+    g5 = np.diag([1.0] * nv + [-1.0] * nv)
+    np.testing.assert_allclose(X, g5 @ np.conj(np.swapaxes(X, -1, -2)) @ g5, atol=1e-13)
+    for mu in range(4):
+        shifted = np.roll(Yb[mu], -1, axis=3 - mu)  # Yb_mu(x + mu) stored at x
+        np.testing.assert_allclose(shifted, g5 @ np.conj(np.swapaxes(Yf[mu], -1, -2)) @ g5, atol=1e-13)
