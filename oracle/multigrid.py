@@ -24,7 +24,8 @@ and vector index on a coarse one.
 
 The coarse operator is also available as the nine-point stencil a GPU kernel would
 apply (coarse_stencil / apply_stencil), read off the Galerkin product column by
-column.
+column, and built locally from the links, the clover and P(x)
+(coarse_stencil_from_links), the construction a GPU kernel would run.
 
 Pins (tests/test_oracle_multigrid.py): orthonormality and chirality of P, the
 gamma_5-hermiticity the coarse operator and its stencil blocks inherit, the stencil
@@ -236,3 +237,60 @@ def apply_stencil(X, Yf, Yb, c):
         out += np.einsum("...ij,...j->...i", Yf[mu], np.roll(v, -1, axis=ax))
         out += np.einsum("...ij,...j->...i", Yb[mu], np.roll(v, +1, axis=ax))
     return out.reshape(shape)
+
+
+def fine_prolongator(P):
+    """P(x) per fine site: (Lt, Lz, Ly, Lx, 12, 2 N_v) on the fine level (blocks are
+    disjoint, so prolonging the unit vector of component j on every coarse site at once
+    gives column j of every site's block)."""
+    n = 2 * P.nv
+    cols = []
+    for j in range(n):
+        e = np.zeros(P.coarse_shape, dtype=np.complex128)
+        e[..., j // P.nv, j % P.nv] = 1.0
+        cols.append(P.prolong(e).reshape(P.fine_shape[:4] + (-1,)))
+    return np.stack(cols, axis=-1)
+
+
+def coarse_stencil_from_links(op, P):
+    """The nine-point coarse stencil built directly from the fine links and clover of a
+    WilsonClover operator -- the local form a GPU kernel evaluates:
+    X(c) = sum_{x in c} P(x)^+ A(x) P(x) + the hops that stay inside block c, and
+    Yf_mu(c) (Yb_mu(c)) = the hops from block c across its upper (lower) face in mu,
+    -kappa w_mu eta P(x)^+ (1 -/+ gamma_mu) U P(x +/- mu)."""
+    from .gamma import GAMMA, ID4
+    from . import lattice as L
+
+    pf = fine_prolongator(P)
+    n = pf.shape[-1]
+    dims = op.dims
+    lt, lz, ly, lx = dims[3], dims[2], dims[1], dims[0]
+    bx, by, bz, bt = P.block
+    bsz = (bx, by, bz, bt)
+    w = op.hop_weights if op.hop_weights is not None else (1.0, 1.0, 1.0, 1.0)
+
+    def to_coarse(field):  # (Lt, Lz, Ly, Lx, n, n) summed over each block
+        return _blocked(field, P.block).sum(axis=(4, 5, 6, 7))
+
+    pdag = np.conj(np.swapaxes(pf, -1, -2))
+    X_fine = pdag @ op.A @ pf
+    X = to_coarse(X_fine)
+    Yf = np.zeros((4,) + X.shape, dtype=np.complex128)
+    Yb = np.zeros_like(Yf)
+    coord = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    for mu in range(4):
+        ax = 3 - mu
+        sf = L.time_boundary_sign(dims, op.t_boundary, True) if mu == 3 else np.ones((lt, lz, ly, lx))
+        sb = L.time_boundary_sign(dims, op.t_boundary, False) if mu == 3 else np.ones((lt, lz, ly, lx))
+        u = op.U[mu]
+        ub = np.conj(np.swapaxes(L.bwd(u, mu), -1, -2))  # U_mu(x - mu)^+
+        hf = np.einsum("st,...ab->...satb", ID4 - GAMMA[mu], u).reshape(u.shape[:4] + (12, 12))
+        hb = np.einsum("st,...ab->...satb", ID4 + GAMMA[mu], ub).reshape(u.shape[:4] + (12, 12))
+        fwd_term = (-op.kappa * w[mu]) * sf[..., None, None] * (pdag @ hf @ L.fwd(pf, mu))
+        bwd_term = (-op.kappa * w[mu]) * sb[..., None, None] * (pdag @ hb @ L.bwd(pf, mu))
+        upper = (coord[ax] % bsz[mu]) == bsz[mu] - 1  # x + mu leaves the block
+        lower = (coord[ax] % bsz[mu]) == 0             # x - mu leaves the block
+        X += to_coarse(np.where(upper[..., None, None], 0, fwd_term) + np.where(lower[..., None, None], 0, bwd_term))
+        Yf[mu] = to_coarse(np.where(upper[..., None, None], fwd_term, 0))
+        Yb[mu] = to_coarse(np.where(lower[..., None, None], bwd_term, 0))
+    return X, Yf, Yb

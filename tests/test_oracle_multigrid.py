@@ -110,3 +110,17 @@ def test_coarse_stencil_equals_galerkin_product():
     for mu in range(4):
         shifted = np.roll(Yb[mu], -1, axis=3 - mu)  # Yb_mu(x + mu) stored at x
         np.testing.assert_allclose(shifted, g5 @ np.conj(np.swapaxes(Yf[mu], -1, -2)) @ g5, atol=1e-13)
+
+
+@pytest.mark.parametrize("aniso", [False, True])
+def test_coarse_stencil_from_links(aniso):
+    """The local construction from links, clover and P(x) equals the stencil read off
+    the Galerkin product (isotropic and anisotropic operators, antiperiodic t)."""
+    dims, block, nv = (6, 6, 6, 6), (2, 2, 2, 2), 2
+    U = L.gauge_from_qdp(W.gauge_links(dims, 0.4, 9), dims)
+    op = dirac.anisotropic(U, 0.1, 2.0, 0.9, 0.8, 1.1) if aniso else dirac.WilsonClover(U, 0.12, 1.2)
+    top = MG.setup(op.M, (6, 6, 6, 6, 4, 3), [block], [nv], [_starts(dims, nv, 70)], relax_steps=3)
+    ref = MG.coarse_stencil(op.M, top.P)
+    got = MG.coarse_stencil_from_links(op, top.P)
+    for a, b in zip(got, ref):
+        np.testing.assert_allclose(a, b, atol=1e-12)
