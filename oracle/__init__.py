@@ -20,6 +20,8 @@ The oracle is a plain, slow, direct transcription of the definitions:
                  and three-point contractions around the solve (Sec. III.A, III.B).
 * ``spectrum`` -- the smallest singular value of the Schur operator (Lanczos on
                  M_hat^+ M_hat), to tell a well-posed workload from a near-singular draw.
+* ``staggered``- the staggered operator of the HISQ action on given fat and long links
+                 (MILC phases), and its CG solve (Sec. II.A, II.E).
 * ``multigrid``- aggregation multigrid preconditioner (null space, block prolongator,
                  Galerkin coarse operator, K-cycle) for flexible GCR (Sec. II.E, III.B).
 
@@ -28,4 +30,4 @@ lexicographic order (Lt, Lz, Ly, Lx, ...), converting to and from the QDP
 layout at the edges.  Which pins check each function is stated in its
 docstring; functions without a pin say "parity unpinned".
 """
-from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum  # noqa: F401
+from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered  # noqa: F401
