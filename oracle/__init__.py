@@ -24,10 +24,13 @@ The oracle is a plain, slow, direct transcription of the definitions:
                  (MILC phases), and its CG solve (Sec. II.A, II.E).
 * ``multigrid``- aggregation multigrid preconditioner (null space, block prolongator,
                  Galerkin coarse operator, K-cycle) for flexible GCR (Sec. II.E, III.B).
+* ``residual`` -- the true residual ||b - M x|| / ||b|| of Eq. 5's operator evaluated one
+                 slab of timeslices at a time (optionally in spawned processes), for
+                 lattices too large for the whole-array evaluation.
 
 Everything is complex128 and operates on whole-lattice arrays in
 lexicographic order (Lt, Lz, Ly, Lx, ...), converting to and from the QDP
 layout at the edges.  Which pins check each function is stated in its
 docstring; functions without a pin say "parity unpinned".
 """
-from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered  # noqa: F401
+from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered, residual  # noqa: F401

@@ -1,12 +1,15 @@
 """Parity at the benchmark's full size, 32^3x64 with 12 right-hand sides, in the
-launch configuration the benchmark times (tuner on), checked on outputs the oracle
-evaluates one site at a time: sampled sites of M_hat x in FP32, FP16 and FP64, and
-the residual b - M x of a 12-source solve at sampled sites."""
+launch configuration the benchmark times (tuner on): sampled sites of M_hat x in FP64,
+FP32, FP16 and BF16 evaluated by the oracle one site at a time; the residual b - M x
+of a 12-source solve at sampled sites; and the true residual ||b - M x|| / ||b|| of
+every right-hand side of the benchmark's solve (FP32 and BF16 inner solvers)
+recomputed by the FP64 oracle over the whole lattice, slab by slab in spawned
+processes."""
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import dirac
+from oracle import dirac, residual
 
 from _gpu import TOL, built, cuda, host
 
@@ -44,7 +47,7 @@ def sampled(field_even, sites):
     return np.array([field_even[t, z, y, x // 2] for x, y, z, t in sites])
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16", "f64"])
 def test_schur_operator_12rhs_sampled(problem, prec):
     pkg, ctx, gauge = problem
     nrhs = 12
@@ -81,3 +84,24 @@ def test_twelve_source_solve_sampled_residual(problem, sloppy, delta):
         bs = np.array([b[k][(x0 + y + z + t) % 2, t, z, y, x0 // 2] for x0, y, z, t in sites])
         res = np.abs(bs - mx).reshape(len(sites), -1).max(axis=1)
         assert res.max() <= 1e-10 * np.linalg.norm(b[k]), (k, res)
+
+
+@pytest.mark.parametrize("sloppy,delta", [("f32", 3e-4), ("bf16", 0.1)])
+def test_twelve_source_solve_full_lattice_oracle_residual(problem, sloppy, delta):
+    """The benchmark's 12-source solve (FP32 inner solver at delta 3e-4, as bench.py runs
+    it) and its BF16 variant: the FP64 oracle recomputes ||b - M x|| / ||b|| of every
+    right-hand side over the whole 32^3x64 lattice, and each is at most the requested
+    1e-10 -- the library's own FP64 number is checked against it as well."""
+    pkg, ctx, gauge = problem
+    b = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
+    x = cuda(np.zeros_like(b))
+    prm = pkg.wcl_default_params(solver="bicgstab", sloppy=sloppy, tol=1e-10, check_every=2, delta_reliable=delta)
+    _, info = ctx.wcl_invert(x, cuda(b), 12, prm)
+    xh = host(x)
+    del x
+    got = residual.true_residuals(gauge, xh, b, DIMS, KAPPA, CSW, t_boundary=-1)
+    assert np.all(got <= 1e-10), (sloppy, got)
+    lib = np.array([i["true_residual"] for i in info])
+    assert all(i["status"] == 0 for i in info), info
+    # the library's FP64 residual agrees with the oracle's to far better than the tolerance
+    assert np.all(np.abs(lib - got) <= 1e-3 * got + 1e-14), (lib, got)

@@ -109,6 +109,39 @@ def test_loss_and_gradient_parity(pkg):
     ctx.close()
 
 
+def test_adam_steps_match_oracle(pkg):
+    """Two training steps on the GPU (its own forward, backward and Adam kernels) against
+    the oracle's loss_and_grad + adam_step in FP64: the weight change of each step agrees
+    to the FP32 tolerance.  Weights start FP32-exact so that both sides start equal; the
+    learning rate is large enough that FP32 rounding of the weights themselves is far
+    below the tolerance."""
+    dims = (4, 4, 2, 4)
+    gauge = W.gauge_links(dims, 0.5, 71)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    ws = [w.astype(np.complex64).astype(np.complex128) for w in ptc.init_weights(seed=72, scale=0.25)]
+    ctx.wcl_precond_load(pkg.ptc_flatten(ws))
+    rs = W.gaussian_fermion(dims, 73, nrhs=4)[:, 0]
+    es = W.gaussian_fermion(dims, 74, nrhs=4)[:, 0]
+    U = L.gauge_from_qdp(gauge, dims)
+    even = L.parity_mask(dims, 0)
+    lr = 0.05
+    state = {}
+    prev = pkg.ptc_flatten(ws)
+    for step, k in enumerate((0, 2)):
+        ctx.wcl_precond_train(cuda(rs[k:k + 2]), cuda(es[k:k + 2]), 2,
+                              pkg.wcl_default_train_params(epochs=1, batch=2, lr=lr))
+        got = ctx.wcl_precond_get()
+        _, g = ptc.loss_and_grad(U, ws, [even_embed(dims, r) for r in rs[k:k + 2]],
+                                 [even_embed(dims, e) for e in es[k:k + 2]], mask=even)
+        ws = ptc.adam_step(ws, g, state, lr=lr)
+        ref = pkg.ptc_flatten(ws)
+        assert relerr(got - prev, ref - prev) <= 1e-5, step
+        ws = pkg.ptc_unflatten(got)  # continue from the GPU's weights
+        prev = got
+    ctx.close()
+
+
 def _pairs(ctx, dims, n, seed):
     """Training pairs (r, e) = (M_hat e, e), e Gaussian on the even sites; r from the GPU operator."""
     import torch

@@ -194,6 +194,59 @@ def test_site_by_site_schur_operator_matches_whole_lattice(dagger):
         np.testing.assert_allclose(v, ref[t, z, y, x], atol=1e-13)
 
 
+# --- slab-by-slab evaluation (oracle.residual) ----------------------------------
+
+@pytest.mark.parametrize("dims,slab,t_boundary", [((4, 2, 6, 8), 3, -1), ((4, 2, 6, 8), 1, -1),
+                                                  ((2, 4, 2, 6), 4, 1), ((4, 2, 2, 2), 1, -1)])
+def test_slabwise_operator_matches_whole_lattice(dims, slab, t_boundary):
+    """The slabs of oracle.residual put together equal WilsonClover.M: ragged last slab,
+    one-timeslice slabs (halo rows on both sides are neighbours), Lt = 2 (both halo rows
+    are the same timeslice), periodic and antiperiodic time."""
+    from oracle import residual
+
+    gq = W.gauge_links(dims, 0.6, 61)
+    psi_q = W.gaussian_fermion(dims, 62)
+    op = dirac.from_qdp_problem(gq, dims, 0.127, 1.3, t_boundary)
+    full = op.M(L.from_qdp(psi_q, dims))
+    got = np.concatenate([residual.M_slab(gq, psi_q, dims, 0.127, 1.3, t0, t1, t_boundary)
+                          for t0, t1 in residual.slabs(dims[3], slab)])
+    np.testing.assert_allclose(got, full, atol=1e-13)
+
+
+def test_slabwise_anisotropic_operator_matches_whole_lattice():
+    from oracle import residual
+
+    dims = (4, 2, 2, 6)
+    gq = W.gauge_links(dims, 0.6, 63)
+    psi_q = W.gaussian_fermion(dims, 64)
+    a = ANISO
+    op = dirac.anisotropic(L.gauge_from_qdp(gq, dims), 0.11, a["xi0"], a["nu"], a["csw_t"], a["csw_r"])
+    full = op.M(L.from_qdp(psi_q, dims))
+    w = a["nu"] / a["xi0"]
+    plane = [a["csw_t"] if nu == 3 else a["csw_r"] / a["xi0"] for _, nu in dirac.PLANES]
+    got = np.concatenate([residual.M_slab(gq, psi_q, dims, 0.11, 0.0, t0, t1, -1, (w, w, w, 1.0), plane)
+                          for t0, t1 in residual.slabs(dims[3], 4)])
+    np.testing.assert_allclose(got, full, atol=1e-13)
+
+
+@pytest.mark.parametrize("processes", [1, 2])
+def test_slabwise_true_residuals(processes):
+    """true_residuals equals the whole-array true_residual for several right-hand sides,
+    serially and in a pool of spawned processes; b = M x gives zero."""
+    from oracle import residual
+
+    dims = (4, 4, 2, 6)
+    gq = W.gauge_links(dims, 0.5, 65)
+    op = dirac.from_qdp_problem(gq, dims, 0.12, 1.0)
+    xs = W.gaussian_fermion(dims, 66, nrhs=3)
+    bs = W.gaussian_fermion(dims, 67, nrhs=3)
+    bs[2] = L.to_qdp(op.M(L.from_qdp(xs[2], dims)), dims)
+    got = residual.true_residuals(gq, xs, bs, dims, 0.12, 1.0, slab=4, processes=processes)
+    ref = [op.true_residual(L.from_qdp(x, dims), L.from_qdp(b, dims)) for x, b in zip(xs, bs)]
+    np.testing.assert_allclose(got[:2], ref[:2], rtol=1e-12)
+    assert got[2] <= 1e-14 and ref[2] <= 1e-14
+
+
 # --- anisotropic form of Eq. 5 --------------------------------------------------
 
 ANISO = dict(xi0=2.464, nu=0.95, csw_t=0.91, csw_r=1.07)  # the parameters of the Sec. III.B example

@@ -172,3 +172,39 @@ def test_restriction_without_conjugate(monkeypatch):
 
     monkeypatch.setattr(multigrid.Prolongator, "restrict", bad)
     _fails(TM.test_prolongator_orthonormal_and_chiral)
+
+
+def test_slab_boundary_sign_not_folded(monkeypatch):
+    """The slab evaluator without the fermion time-boundary sign on the t links."""
+    from oracle import residual
+
+    orig = residual.slab_operator
+    monkeypatch.setattr(residual, "slab_operator",
+                        lambda g, dims, k, c, t0, t1, tb=-1, hw=None, pc=None: orig(g, dims, k, c, t0, t1, 1, hw, pc))
+    _fails(TD.test_slabwise_operator_matches_whole_lattice, (4, 2, 6, 8), 3, -1)
+
+
+def test_adam_without_bias_correction(monkeypatch):
+    def bad(weights, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        state["t"] = state.get("t", 0) + 1
+        out = []
+        for i, (Wt, g) in enumerate(zip(weights, grads)):
+            gr = np.stack([g.real, g.imag])
+            m = state.setdefault(("m", i), np.zeros_like(gr))
+            v = state.setdefault(("v", i), np.zeros_like(gr))
+            m[:] = b1 * m + (1 - b1) * gr
+            v[:] = b2 * v + (1 - b2) * gr * gr
+            upd = lr * m / (np.sqrt(v) + eps)
+            out.append(Wt - (upd[0] + 1j * upd[1]))
+        return out
+
+    monkeypatch.setattr(ptc, "adam_step", bad)
+    _fails(TP.test_adam_two_steps_closed_form)
+
+
+def test_adam_second_moment_of_the_wrong_step(monkeypatch):
+    """The second moment bias-corrected with b1 instead of b2."""
+    orig = ptc.adam_step
+    monkeypatch.setattr(ptc, "adam_step", lambda w, g, s, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8:
+                        orig(w, g, s, lr=lr, b1=b1, b2=b1, eps=eps))
+    _fails(TP.test_adam_two_steps_closed_form)

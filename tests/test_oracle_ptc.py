@@ -132,3 +132,32 @@ def test_adam_reduces_loss():
         ws = ptc.adam_step(ws, g, state, lr=1e-2)
         l1, g = ptc.loss_and_grad(U, ws, rs, es)
     assert l1 < 0.5 * l0
+
+
+def test_adam_two_steps_closed_form():
+    """Two Adam steps on L = sum |W|^2 (G = dL/dRe W + i dL/dIm W = 2 W) from W = 1 + 2i,
+    written out from the update rule with bias correction (Kingma & Ba 2015, Algorithm 1)
+    on the real and imaginary parts separately:
+      step 1: m = (1-b1) g, v = (1-b2) g^2, m/(1-b1) = g, v/(1-b2) = g^2,
+              W1 = W0 - lr g / (|g| + eps)
+      step 2: m = b1 (1-b1) g1 + (1-b1) g2, v = b2 (1-b2) g1^2 + (1-b2) g2^2,
+              W2 = W1 - lr (m / (1-b1^2)) / (sqrt(v / (1-b2^2)) + eps)."""
+    lr, b1, b2, eps = 0.1, 0.9, 0.999, 1e-8
+    w0 = np.array([1.0 + 2.0j])
+    state = {}
+    w1 = ptc.adam_step([w0], [2 * w0], state, lr=lr, b1=b1, b2=b2, eps=eps)[0]
+    # step 1 by hand: g = (2, 4)
+    e1 = (1.0 - 0.1 * 2.0 / (2.0 + 1e-8)) + 1j * (2.0 - 0.1 * 4.0 / (4.0 + 1e-8))
+    assert abs(w1[0] - e1) <= 1e-15
+    w2 = ptc.adam_step([w1], [2 * w1], state, lr=lr, b1=b1, b2=b2, eps=eps)[0]
+    # step 2 by hand: g1 = (2, 4), g2 = 2 * w1 = (1.8, 3.8) up to the eps terms
+    g2r, g2i = 2 * e1.real, 2 * e1.imag
+    mr = (0.9 * 0.1 * 2.0 + 0.1 * g2r) / (1 - 0.81)
+    mi = (0.9 * 0.1 * 4.0 + 0.1 * g2i) / (1 - 0.81)
+    vr = (0.999 * 0.001 * 4.0 + 0.001 * g2r ** 2) / (1 - 0.998001)
+    vi = (0.999 * 0.001 * 16.0 + 0.001 * g2i ** 2) / (1 - 0.998001)
+    e2 = (e1.real - 0.1 * mr / (np.sqrt(vr) + 1e-8)) + 1j * (e1.imag - 0.1 * mi / (np.sqrt(vi) + 1e-8))
+    assert abs(w2[0] - e2) <= 1e-14
+    # the numbers themselves: first step moves each part by lr, the second by about lr
+    assert abs(w1[0] - (0.9 + 1.9j)) <= 1e-8
+    assert abs(w2[0] - (0.800412 + 1.800166j)) <= 1e-6
