@@ -364,16 +364,21 @@ wcl_status wcl_get_stats(wcl_ctx* ctx, wcl_stats* out, int reset);
  * beforehand with wcl_create / wcl_load_gauge.
  *
  * Scratch: the input copy, the odd-parity intermediate and the output live in
- * one fixed device array of 3 x 192 x WCL_NOALLOC_MAX_VH bytes (9 MiB) that
- * every GPU which loads the library holds until the process exits.  Lattices
- * with more than WCL_NOALLOC_MAX_VH padded sites per parity are rejected with
- * WCL_ERR_INVALID_ARG.  The first call on each device looks up the array's
- * device address once (with that device current); make that first call before
- * any stream capture.  Every call shares the array and leaves its contents
+ * one fixed device array of 3 x 192 x WCL_NOALLOC_MAX_VH bytes (9 MiB).  It is
+ * set up -- its device address looked up, which loads the library module that
+ * holds it -- by wcl_create, so every GPU on which a context has been created
+ * holds it until the process exits, and the call itself allocates nothing, also
+ * the first time and on a lattice shape it has not seen (the autotuner is not
+ * consulted beyond its cache: an untuned configuration runs its default kernel).
+ * A cudaDeviceReset invalidates it together with every context of that device.
+ * Lattices with more than WCL_NOALLOC_MAX_VH padded sites per parity are rejected
+ * with WCL_ERR_INVALID_ARG.  Every call shares the array and leaves its contents
  * behind (each call writes everything it reads, so nothing is cleared); calls
  * whose GPU work overlaps -- from different streams, threads or contexts on the
  * same device -- race on it and must be serialised by the caller.
- *   d_in_e, d_out_e: device, [Lt][Lz][Ly][Lx/2][4][3] complex128, caller-owned. */
+ *   d_in_e, d_out_e: device memory of the context's GPU, [Lt][Lz][Ly][Lx/2][4][3]
+ *   complex128, caller-owned; anything else (page-locked or pageable host memory,
+ *   another GPU's memory) is WCL_ERR_INVALID_ARG. */
 wcl_status wcl_apply_Mpc_noalloc(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, int dagger);
 
 /* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */

@@ -203,6 +203,9 @@ wcl_status wcl_create(wcl_ctx** out, const int dims[4], int t_boundary, int devi
     e = cudaMalloc(&c->d_flags, 64);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_flags, 64);
     if (e != cudaSuccess) { s = cuda_fail(e, "flag buffers"); break; }
+    // the fixed scratch of wcl_apply_Mpc_noalloc is looked up (its module loaded) here,
+    // where allocating is allowed, not inside that call
+    s = noalloc_prepare(device);
   } while (0);
   if (s != WCL_OK) {
     wcl_destroy(c);

@@ -186,5 +186,10 @@ void profile_flush(wcl_ctx* c, size_t from = 0);
 void profile_accum_range(wcl_ctx* c, size_t from, size_t to);
 // pinned host buffer, grown on demand
 wcl_status hws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out);
+// device address of wcl_apply_Mpc_noalloc's fixed scratch array, looked up once per
+// device with that device current (loads its module, which allocates the array)
+wcl_status noalloc_prepare(int device);
+// load the module of the FP64 per-thread dslash kernels (dslash_f64.cu) without a launch
+cudaError_t load_dslash_f64_module();
 
 }  // namespace wcl
