@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--staged-spinors", type=int, default=0,
                     help="--case mhat: multi-RHS kernel with cp.async-staged neighbour spinors (tuner off)")
     ap.add_argument("--autotune", type=int, default=1, help="--case mhat: dslash autotuner on/off")
+    ap.add_argument("--paired-rhs", type=int, default=0,
+                    help="--case mhat: packed-pair multi-RHS kernel (two RHS per thread, FFMA2) when the tuner is off")
+    ap.add_argument("--blocked-tiles", type=int, default=0, help="--case mhat: z-blocked tile order (tuner off)")
     return ap.parse_args()
 
 
@@ -416,6 +419,8 @@ def run_mhat_case(args):
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_SHARED_LINKS, args.shared_links)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_STAGED_SPINORS, args.staged_spinors)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_AUTOTUNE, args.autotune)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_PAIRED_RHS, args.paired_rhs)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_BLOCKED_TILES, args.blocked_tiles)
     ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, SEED)).cuda(), KAPPA, CSW)
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     psi = torch.from_numpy(W.gaussian_fermion(dims, 1, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(-1)
@@ -433,6 +438,7 @@ def run_mhat_case(args):
     print(json.dumps({"case": "mhat", "lattice": dims, "nrhs": args.nrhs, "prec": args.prec,
                       "tensor_cores": args.tensor_cores, "shared_links": args.shared_links,
                       "staged_spinors": args.staged_spinors, "autotune": args.autotune,
+                      "paired_rhs": args.paired_rhs, "blocked_tiles": args.blocked_tiles,
                       "dslash_launches": st["dslash_timed"], "avg_launch_ms": st["dslash_ms"] / st["dslash_timed"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind}))
     ctx.close()

@@ -320,6 +320,19 @@ typedef enum {
                                slice, so that the t neighbours of a site are still in L2 (DRAM
                                traffic 1.07x instead of 1.25x the algorithmic bytes at 32^3x64);
                                0 (default): site order.  With the tuner on, both are candidates. */
+  ,
+  WCL_OPT_PAIRED_RHS = 7 /* 1: when the tuner is off, the multi-RHS FP32 / 16-bit dslash (4..16 RHS)
+                            runs the packed-pair kernel: each thread owns one site and two
+                            right-hand sides held in float2 registers, so that one packed FP32
+                            instruction (FFMA2 / FADD2) serves both; the tile is that of
+                            WCL_OPT_SHARED_LINKS (or 16 with WCL_OPT_BLOCKED_TILES).  0 (default):
+                            one right-hand side per thread.  With the tuner on, both are candidates. */
+  ,
+  WCL_OPT_PREFETCH_SPINORS = 8 /* 1: when the tuner is off, the multi-RHS FP32 / 16-bit dslash (16-site
+                                  tiles, one right-hand side per thread) loads the neighbour spinor
+                                  of the next hop into registers before computing the current one,
+                                  so that one hop's gathers are always in flight; 0 (default): each
+                                  hop loads and then computes.  With the tuner on, both are candidates. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

@@ -125,6 +125,10 @@ bool use_mrhs(const wcl_ctx* c, int prec, int nrhs, int mode) {
          (mode == MODE_POST || mode == (MODE_XPAY | MODE_PRE));
 }
 
+bool use_pair(const wcl_ctx* c, int prec, int nrhs, int mode) {
+  return use_mrhs(c, prec, nrhs, mode) && (prec == F32 || prec == F16 || prec == BF16);
+}
+
 int dslash_max_chunks(const std::vector<wcl_ctx*>& ctxs, int prec) {
   // smallest site tile any dslash variant may use, so that the partials fit every variant
   (void)prec;
@@ -166,16 +170,26 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   a.b = make_batch(ctxs, 1, ts, 0);
   for (size_t l = 0; l < ctxs.size(); l++) {
     a.b.lat[l].slot_base = (int)l * nrhs;
-    if (ch.variant == V_SMEM_ZB) a.b.lat[l].zblk = mrhs_zblock(a.b.lat[l], ts);
+    if (ch.variant == V_SMEM_ZB || ch.variant == V_PAIR_ZB || ch.variant == V_SMEM_PF_ZB)
+      a.b.lat[l].zblk = mrhs_zblock(a.b.lat[l], ts);
   }
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
+  if (ch.variant == V_PAIR || ch.variant == V_PAIR_ZB) {
+    switch (prec) {
+      case F32: return launch_dslash_pair<F32>(a, dagger, mode, ts, st);
+      case F16: return launch_dslash_pair<F16>(a, dagger, mode, ts, st);
+      case BF16: return launch_dslash_pair<BF16>(a, dagger, mode, ts, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   const bool async = ch.variant == V_SMEM_ASYNC;
+  const bool pf = ch.variant == V_SMEM_PF || ch.variant == V_SMEM_PF_ZB;
   switch (prec) {
-    case F64: return launch_dslash_mrhs<F64>(a, dagger, mode, ts, st, async);
-    case F32: return launch_dslash_mrhs<F32>(a, dagger, mode, ts, st, async);
-    case F16: return launch_dslash_mrhs<F16>(a, dagger, mode, ts, st, async);
-    default: return launch_dslash_mrhs<BF16>(a, dagger, mode, ts, st, async);
+    case F64: return launch_dslash_mrhs<F64>(a, dagger, mode, ts, st, async, pf);
+    case F32: return launch_dslash_mrhs<F32>(a, dagger, mode, ts, st, async, pf);
+    case F16: return launch_dslash_mrhs<F16>(a, dagger, mode, ts, st, async, pf);
+    default: return launch_dslash_mrhs<BF16>(a, dagger, mode, ts, st, async, pf);
   }
 }
 
@@ -193,18 +207,24 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   const int nlat = (int)ctxs.size();
   const bool tc_ok = use_tc(c0, prec, nrhs, mode);
   const bool mr_ok = use_mrhs(c0, prec, nrhs, mode);
+  const bool pair_ok = use_pair(c0, prec, nrhs, mode);
   TuneChoice dflt{V_THREAD, c0->dslash_block[prec == DF64 ? F64 : prec]};
   if (tc_ok)
     dflt = {V_TC, tc_tile_sites()};
+  else if (pair_ok && c0->paired_rhs)
+    dflt = c0->blocked_tiles ? TuneChoice{V_PAIR_ZB, 16} : TuneChoice{V_PAIR, c0->shared_links};
   else if (mr_ok && c0->staged_spinors && prec != F64)
     dflt = {V_SMEM_ASYNC, 16};
+  else if (mr_ok && c0->prefetch_spinors && prec != F64)
+    dflt = c0->blocked_tiles ? TuneChoice{V_SMEM_PF_ZB, 16} : TuneChoice{V_SMEM_PF, 16};
   else if (mr_ok && c0->blocked_tiles)
     dflt = {V_SMEM_ZB, 16};
   else if (mr_ok)
     dflt = {V_SMEM, prec == F64 ? 16 : c0->shared_links};
   std::string key = "dslash p" + std::to_string(prec) + " m" + std::to_string(mode) + " d" + std::to_string(dagger) +
                     " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok) +
-                    std::to_string((int)c0->staged_spinors) + std::to_string((int)c0->blocked_tiles);
+                    std::to_string((int)c0->staged_spinors) + std::to_string((int)c0->blocked_tiles) +
+                    std::to_string((int)c0->paired_rhs) + std::to_string((int)c0->prefetch_spinors);
   for (auto* c : ctxs)
     key += " " + std::to_string(c->lat.dims[0]) + "x" + std::to_string(c->lat.dims[1]) + "x" +
            std::to_string(c->lat.dims[2]) + "x" + std::to_string(c->lat.dims[3]);
@@ -225,6 +245,7 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
     if (prec != F64) {
       cand.push_back({V_SMEM, 32});  // FP64 32-site tiles exceed 48 KB of static shared memory
       cand.push_back({V_SMEM_ASYNC, 16});
+      cand.push_back({V_SMEM_PF, 16});
     }
     bool zb = false;
     for (auto* c : ctxs) {
@@ -235,6 +256,11 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
       zb = zb || mrhs_zblock(gg, 16) > 0;
     }
     if (zb) cand.push_back({V_SMEM_ZB, 16});
+    if (zb && prec != F64) cand.push_back({V_SMEM_PF_ZB, 16});
+    if (pair_ok) {
+      for (int ts : {8, 16, 32}) cand.push_back({V_PAIR, ts});
+      if (zb) cand.push_back({V_PAIR_ZB, 16});
+    }
   }
   if (tc_ok) cand.push_back({V_TC, tc_tile_sites()});
   const int plain_mode = mode & 31;  // without the fused reduction

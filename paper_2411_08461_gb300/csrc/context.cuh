@@ -62,6 +62,8 @@ struct wcl_ctx {
   bool ptc_tensor_cores = true;  // BF16 network layers mix channels on the tensor cores
   bool staged_spinors = false;   // untuned multi-RHS dslash: cp.async-staged neighbour spinors
   bool blocked_tiles = false;    // untuned multi-RHS dslash: tiles in z blocks (large lattices)
+  bool paired_rhs = false;       // untuned multi-RHS FP32/16-bit dslash: the packed-pair kernel
+  bool prefetch_spinors = false; // untuned multi-RHS dslash: next hop's spinor prefetched in registers
   int blas_block = 256;
 };
 
@@ -157,7 +159,14 @@ bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
 // kept for the process; with WCL_TUNE_CACHE=<file> choices persist across runs.
 // V_SMEM_ZB: the shared-memory kernel walking its tiles in z blocks (L2 reuse of the
 // t neighbours on large lattices)
-enum TuneVariant { V_THREAD = 0, V_SMEM = 1, V_TC = 2, V_SMEM_ASYNC = 3, V_SMEM_ZB = 4 };
+// V_PAIR / V_PAIR_ZB: the packed-pair kernel (dslash_pair.cuh: two right-hand sides per
+// thread in float2 registers, FFMA2), in site order / z-blocked tile order
+// V_SMEM_PF / V_SMEM_PF_ZB: the shared-memory kernel with the next hop's neighbour spinor
+// loaded into registers while the current hop is computed
+enum TuneVariant {
+  V_THREAD = 0, V_SMEM = 1, V_TC = 2, V_SMEM_ASYNC = 3, V_SMEM_ZB = 4, V_PAIR = 5, V_PAIR_ZB = 6, V_SMEM_PF = 7,
+  V_SMEM_PF_ZB = 8
+};
 struct TuneChoice {
   int variant;  // TuneVariant
   int block;    // threads per CTA (V_THREAD) or sites per CTA (V_SMEM, V_SMEM_ASYNC, V_TC)
@@ -173,6 +182,10 @@ template <int P>
 cudaError_t launch_dslash(const DslashArgs& a, bool dagger, int mode, int block, cudaStream_t st);
 template <int P>
 cudaError_t launch_clover(const CloverArgs& a, int block, cudaStream_t st);
+// packed-pair multi-RHS kernel (FP32 and 16-bit storage; defined in dslash_<prec>.cu)
+template <int P>
+cudaError_t launch_dslash_pair(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st);
+bool use_pair(const wcl_ctx* c, int prec, int nrhs, int mode);
 
 // caller-owned QDP fields of a solve, one pointer per lattice
 struct SolveIO {

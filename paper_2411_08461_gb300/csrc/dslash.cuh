@@ -712,9 +712,13 @@ struct MrhsBounds<32> {
 // ASYNC: the eight neighbour spinors of a thread are staged through shared memory
 // with cp.async, two hops in flight (dynamic shared memory: 2 stages x CH chunks x
 // blockDim 16-byte slots, plus norms)
-template <int P, bool DAG, int MODE, int EPI, int TS, bool ASYNC = false>
+// PF: the neighbour spinor of the next hop is loaded into registers before the current
+// hop is computed (software pipelining: one hop's gathers always in flight), with the
+// register cap of the staged variant
+template <int P, bool DAG, int MODE, int EPI, int TS, bool ASYNC = false, bool PF = false>
 __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
-                                  (P == F64 ? 1 : ASYNC ? MrhsBounds<TS>::MIN_BLOCKS - 1 : MrhsBounds<TS>::MIN_BLOCKS))
+                                  (P == F64 ? 1 : (ASYNC || PF) ? MrhsBounds<TS>::MIN_BLOCKS - 1
+                                                                : MrhsBounds<TS>::MIN_BLOCKS))
     dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
   using R = typename Traits<P>::R;
   constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
@@ -856,6 +860,27 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
           cp_async_commit();
         }
       }
+    } else if constexpr (PF) {
+      cpx<R> nxt[12];
+      SpinorIO<P>::load(nxt, in, in_norm, stride, Nb[0][ls]);
+#pragma unroll
+      for (int hh = 0; hh < 8; hh++) {
+        cpx<R> psi[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) psi[k] = nxt[k];
+        if (hh < 7) SpinorIO<P>::load(nxt, in, in_norm, stride, Nb[hh + 1][ls]);
+        const R sign = hh == 6 ? sf : hh == 7 ? sb : R(1);
+        switch (hh) {
+          case 0: hop_from<0, false, DAG>(acc, psi, Us[0][ls], sign); break;
+          case 1: hop_from<0, true, DAG>(acc, psi, Us[1][ls], sign); break;
+          case 2: hop_from<1, false, DAG>(acc, psi, Us[2][ls], sign); break;
+          case 3: hop_from<1, true, DAG>(acc, psi, Us[3][ls], sign); break;
+          case 4: hop_from<2, false, DAG>(acc, psi, Us[4][ls], sign); break;
+          case 5: hop_from<2, true, DAG>(acc, psi, Us[5][ls], sign); break;
+          case 6: hop_from<3, false, DAG>(acc, psi, Us[6][ls], sign); break;
+          default: hop_from<3, true, DAG>(acc, psi, Us[7][ls], sign); break;
+        }
+      }
     } else {
       hop_dir_smem<P, 0, DAG>(acc, in, in_norm, stride, Nb[0][ls], Nb[1][ls], Us[0][ls], Us[1][ls], R(1), R(1));
       hop_dir_smem<P, 1, DAG>(acc, in, in_norm, stride, Nb[2][ls], Nb[3][ls], Us[2][ls], Us[3][ls], R(1), R(1));
@@ -976,7 +1001,7 @@ inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_
 
 template <int P>
 cudaError_t launch_dslash_mrhs(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st,
-                               bool async = false);
+                               bool async = false, bool pf = false);
 
 // dynamic shared memory of the staged variant for `threads` threads
 template <int P>
@@ -996,7 +1021,9 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes) {
       cudaError_t ea = allow_dynamic_smem(dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, true>, sm); \
       if (ea != cudaSuccess) return ea;                                                         \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, true><<<a.b.total_blocks, threads, sm, st>>>(a); \
-    } else if (ts == 32)                                                                        \
+    } else if (pf)                                                                              \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, false, true><<<a.b.total_blocks, threads, 0, st>>>(a); \
+    else if (ts == 32)                                                                          \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 32><<<a.b.total_blocks, threads, 0, st>>>(a);       \
     else if (ts == 8)                                                                           \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 8><<<a.b.total_blocks, threads, 0, st>>>(a);        \
@@ -1008,8 +1035,9 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes) {
 // ts: sites per CTA (8, 16 or 32); the geometry a.b must have been built with that tile
 #define WCL_DEFINE_MRHS_LAUNCHER(P)                                                              \
   template <>                                                                                    \
-  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st, bool async) { \
-    if (async && ts != 16) return cudaErrorInvalidValue;                                         \
+  cudaError_t launch_dslash_mrhs<P>(const DslashArgs& a, bool dagger, int mode, int ts, cudaStream_t st, bool async, \
+                                    bool pf) {                                                   \
+    if ((async || pf) && ts != 16) return cudaErrorInvalidValue;                                 \
     const int threads = (ts * a.nrhs_tc + 31) / 32 * 32;                                         \
     int fin = 0;                                                                                 \
     switch (mode | (dagger ? 16 : 0)) {                                                          \

@@ -29,6 +29,8 @@ WCL_OPT_AUTOTUNE = 3
 WCL_OPT_PTC_TENSOR_CORES = 4
 WCL_OPT_STAGED_SPINORS = 5
 WCL_OPT_BLOCKED_TILES = 6
+WCL_OPT_PAIRED_RHS = 7
+WCL_OPT_PREFETCH_SPINORS = 8
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 

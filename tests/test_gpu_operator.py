@@ -155,6 +155,50 @@ def test_apply_Mpc_multi_rhs_shared_links(pkg, dims, nrhs, dagger, prec, tile):
     ctx.close()
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((2, 2, 2, 2), 16), ((8, 4, 4, 6), 7)])
+def test_apply_Mpc_multi_rhs_paired(pkg, dims, nrhs, dagger, prec, tile):
+    """The packed-pair kernel (two right-hand sides per thread in float2 registers, FFMA2):
+    8-, 16- and 32-site tiles, ragged last tile for Vh = 96, 1296, 8, 384, an odd RHS count
+    (the last pair holds one right-hand side) and RHS of very different size."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_PAIRED_RHS, WCL_OPT_SHARED_LINKS
+
+    ctx, op, _ = _setup(pkg, dims, seed=27)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_SHARED_LINKS, tile)
+    ctx.wcl_set_option(WCL_OPT_PAIRED_RHS, 1)
+    psi = W.gaussian_fermion(dims, 28, nrhs=nrhs)[:, 0].copy()
+    psi[1] *= 1e-7
+    psi[nrhs - 1] *= 1e5
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs, dagger=dagger)
+    got = host(out)
+    for k in range(nrhs):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL[prec], k
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_multi_rhs_paired_blocked_tile_order(pkg, prec):
+    """The packed-pair kernel walking its 16-site tiles in blocks of z planes (32x24x24x4)."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_BLOCKED_TILES, WCL_OPT_PAIRED_RHS
+
+    dims = (32, 24, 24, 4)
+    ctx, op, _ = _setup(pkg, dims, seed=29)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_BLOCKED_TILES, 1)
+    ctx.wcl_set_option(WCL_OPT_PAIRED_RHS, 1)
+    psi = W.gaussian_fermion(dims, 30, nrhs=6)[:, 0].copy()
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=6)
+    got = host(out)
+    for k in range(6):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], False)) <= TOL[prec], k
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_shared_links_and_per_thread_kernels_agree(pkg, prec):
     from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS
@@ -193,7 +237,7 @@ def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
     assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
     for v, b, ms, *_ in lines:
         assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32), (3, 16),
-                                    (4, 16)}
+                                    (4, 16), (5, 8), (5, 16), (5, 32), (6, 16), (7, 16), (8, 16)}
         assert float(ms) > 0
 
 
@@ -208,6 +252,29 @@ def test_apply_Mpc_multi_rhs_staged_spinors(pkg, dims, nrhs, dagger, prec):
     ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
     ctx.wcl_set_option(WCL_OPT_STAGED_SPINORS, 1)
     psi = W.gaussian_fermion(dims, 24, nrhs=nrhs)[:, 0].copy()
+    psi[1] *= 1e-7
+    out = cuda(np.zeros_like(psi))
+    ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs, dagger=dagger)
+    got = host(out)
+    for k in range(nrhs):
+        assert relerr(got[k], dirac.apply_Mhat_qdp(op, psi[k], dagger)) <= TOL[prec], k
+    ctx.close()
+
+
+@pytest.mark.parametrize("blocked", [0, 1])
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 2, 8), 12), ((6, 6, 6, 8), 4), ((8, 4, 4, 6), 7), ((32, 24, 24, 4), 5)])
+def test_apply_Mpc_multi_rhs_prefetched_spinors(pkg, dims, nrhs, dagger, prec, blocked):
+    """Multi-RHS kernel that loads the next hop's neighbour spinor into registers while it
+    computes the current hop, in site order and in z-blocked tile order."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_BLOCKED_TILES, WCL_OPT_PREFETCH_SPINORS
+
+    ctx, op, _ = _setup(pkg, dims, seed=31)
+    ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    ctx.wcl_set_option(WCL_OPT_PREFETCH_SPINORS, 1)
+    ctx.wcl_set_option(WCL_OPT_BLOCKED_TILES, blocked)
+    psi = W.gaussian_fermion(dims, 32, nrhs=nrhs)[:, 0].copy()
     psi[1] *= 1e-7
     out = cuda(np.zeros_like(psi))
     ctx.wcl_apply_Mpc(out, cuda(psi), prec, nrhs=nrhs, dagger=dagger)

@@ -100,14 +100,29 @@ def test_batch_of_uneven_lattices(pkg):
         c.close()
 
 
-@pytest.mark.parametrize("shared_links", [8, 16, 32, 0, "staged"])
+@pytest.mark.parametrize("shared_links", [8, 16, 32, 0, "staged", "prefetch", "paired8", "paired16", "paired32"])
 @pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
 def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
-    """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials)."""
-    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_SHARED_LINKS, WCL_OPT_STAGED_SPINORS
+    """Two lattices x 4 RHS: the multi-RHS dslash and its fused reductions (per-tile partials),
+    with one RHS per thread or two (the packed-pair kernel)."""
+    _batch_solve(pkg, solver, shared_links, nrhs=4, sloppy="f32")
+
+
+@pytest.mark.parametrize("sloppy", ["f32", "bf16", "f16"])
+def test_batch_of_lattices_paired_odd_rhs(pkg, sloppy):
+    """Five RHS through the packed-pair kernel (the last pair holds one right-hand side) with
+    its fused BiCGStab reductions, in FP32 and 16-bit storage."""
+    _batch_solve(pkg, "bicgstab", "paired16", nrhs=5, sloppy=sloppy)
+
+
+def _batch_solve(pkg, solver, shared_links, nrhs, sloppy):
+    from paper_2411_08461_gb300.wcl import (WCL_OPT_AUTOTUNE, WCL_OPT_PAIRED_RHS, WCL_OPT_PREFETCH_SPINORS,
+                                            WCL_OPT_SHARED_LINKS, WCL_OPT_STAGED_SPINORS)
 
     staged = shared_links == "staged"
-    shared_links = 16 if staged else shared_links
+    prefetch = shared_links == "prefetch"
+    paired = isinstance(shared_links, str) and shared_links.startswith("paired")
+    shared_links = 16 if (staged or prefetch) else int(shared_links[6:]) if paired else shared_links
 
     shapes = [(4, 4, 4, 8), (6, 6, 2, 10)]
     ctxs, ops, bs, xs = [], [], [], []
@@ -117,18 +132,20 @@ def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
         c.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
         c.wcl_set_option(WCL_OPT_SHARED_LINKS, shared_links)
         c.wcl_set_option(WCL_OPT_STAGED_SPINORS, int(staged))
+        c.wcl_set_option(WCL_OPT_PAIRED_RHS, int(paired))
+        c.wcl_set_option(WCL_OPT_PREFETCH_SPINORS, int(prefetch))
         c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
         ctxs.append(c)
         ops.append(dirac.from_qdp_problem(g, dims, 0.1235, 1.0))
-        b = W.z2_fermion(dims, 40 + k, nrhs=4)
+        b = W.z2_fermion(dims, 40 + k, nrhs=nrhs)
         b[2] *= 1e3
         bs.append(b)
         xs.append(cuda(np.zeros_like(b)))
-    _, info = pkg.wcl_invert_batch(ctxs, xs, [cuda(b) for b in bs], 4,
-                                   pkg.wcl_default_params(solver=solver, sloppy="f32", tol=1e-10))
+    _, info = pkg.wcl_invert_batch(ctxs, xs, [cuda(b) for b in bs], nrhs,
+                                   pkg.wcl_default_params(solver=solver, sloppy=sloppy, tol=1e-10))
     for k in range(len(shapes)):
         xh = host(xs[k])
-        for r in range(4):
+        for r in range(nrhs):
             assert _oracle_true_residual(ops[k], xh[r], bs[k][r]) <= 1e-10, (k, r, info)
     for c in ctxs:
         c.close()
