@@ -41,7 +41,12 @@ EPS, SEED, KAPPA, CSW, TOL = 0.3, 0, 0.1235, 1.0, 1e-10
 METRIC = "clover dslash GB/s & roofline %; 12-RHS solve time to 1e-10 true residual"
 PREC_INDEX = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 vector rate, nominal
-TRAFFIC_F32_32C64_12RHS = (2 * 3.86e9 + 5.90e9 + 4.64e9) / 4  # measured DRAM bytes per launch (see run_ours)
+# DRAM bytes (read + written) per site and right-hand side of the 12-RHS FP32 fused dslash,
+# averaged over the solve's launch mix (2 x A^-1 D x, 1 x alpha-fused, 1 x omega-fused), from
+# one ncu capture of 8 such launches of the same solve on 32^3x16 -- the bench lattice's
+# spatial volume, so the t neighbours lie as far apart as at 32^3x64, with a few GB on the
+# device: 978/1158/943/1472 MB per launch for 3.15 M site-RHS, 361.7 B against 320 algorithmic
+TRAFFIC_F32_12RHS_PER_SITE_RHS = 361.7
 UNIT = "12-RHS solves/s"
 WORKLOAD = "32^3x64 Wilson-clover, eps 0.3, kappa 0.1235, c_sw 1.0, 12 spin-colour point sources, tol 1e-10"
 
@@ -223,6 +228,24 @@ def cpu_baseline_sample(gpu_iters_per_rhs: float, budget_s: float = 20.0):
                       f"kernels are single-threaded"}
 
 
+def oracle_true_residuals(gauge, x, b, dims):
+    """||b - M x|| / ||b|| per right-hand side by the FP64 oracle over the whole lattice,
+    slab by slab in a pool of spawned processes (one per host core, at most 16)."""
+    import numpy as np
+
+    from oracle import residual
+
+    procs = min(16, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    r = residual.true_residuals(gauge, x, b, dims, KAPPA, CSW, t_boundary=-1, processes=procs)
+    sec = time.perf_counter() - t0
+    return {"worst": float(np.max(r)), "per_rhs": [float(v) for v in r], "seconds": sec, "processes": procs,
+            "seconds_per_rhs": sec / len(r),
+            "what": f"FP64 oracle: M x on the whole {'x'.join(map(str, dims))} lattice for each of the "
+                    f"{len(r)} solutions (4-timeslice slabs with one halo timeslice each side, clover built "
+                    f"per slab), ||b - M x|| / ||b||"}
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: each step is one bounded sample (oracle
     BiCGStab iterations on 16^3x32, scaled to a 12-RHS 32^3x64 solve)."""
@@ -267,7 +290,6 @@ def run_ours(args, rank, world, local):
     src = np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])
     ctx = pkg.Context(dims, t_boundary=-1, device=local, stream=stream)
     ctx.wcl_load_gauge(torch.from_numpy(gauge).to(dev), KAPPA, CSW)
-    del gauge
     b = torch.from_numpy(src).to(dev)
     x = torch.zeros_like(b)
     prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=TOL, check_every=args.check_every,
@@ -296,6 +318,26 @@ def run_ours(args, rank, world, local):
     worst = max(i["true_residual"] for i in infos)
     assert worst <= TOL and all(i["status"] == 0 for i in infos), infos
     iters = statistics.mean(i["iters"] for i in infos)
+
+    # the comparison method on the same GPU and workload: plain FP32 single-RHS BiCGStab,
+    # twelve sequential solves restarted from the IEEE FP64 true residual (pure FP32 stalls
+    # near 1e-7), timed with CUDA events like the batched solve
+    plain = pkg.wcl_default_params(sloppy="f32", outer="f64", tol=TOL, restart_on_update=1, delta_reliable=1e-5)
+    xp = torch.zeros_like(b)
+    ctx.wcl_invert(xp[:1], b[:1], 1, plain)  # warm-up of the single-RHS configurations
+    p_runs, p_infos = [], []
+    for _ in range(max(1, min(args.steps, 2))):
+        barrier(world)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        p_infos = [ctx.wcl_invert(xp[k:k + 1], b[k:k + 1], 1, plain)[1][0] for k in range(12)]
+        q1.record(stream)
+        torch.cuda.synchronize()
+        p_runs.append(q0.elapsed_time(q1))
+    plain_ms = max_over_ranks(statistics.median(p_runs), world)
+    assert all(i["status"] == 0 and i["true_residual"] <= TOL for i in p_infos), p_infos
+    del xp
 
     # one more solve with every dslash launch timed by events (direct launches, no graphs)
     ctx.wcl_set_profiling(True)
@@ -352,15 +394,11 @@ def run_ours(args, rank, world, local):
     df_ms, df_n = st["prec_ms"][4], st["prec_timed"][4]
     f64_gflops = f64["dslash_flops"] / (f64["dslash_ms"] * 1e-3) / 1e9 if f64["dslash_ms"] > 0 else None
     f32_gbs = f32["dslash_bytes"] / (f32["dslash_ms"] * 1e-3) / 1e9 if f32["dslash_ms"] > 0 else None
-    # DRAM bytes (read + written) per inner-dslash launch of this solve, averaged over
-    # its launch mix (2 x A^-1 D, 1 x alpha-fused, 1 x omega-fused per iteration), from
-    # an ncu capture of the same launches at 32^3x64, 12 RHS, FP32 (1 pass,
-    # dram__bytes_read.sum + dram__bytes_write.sum): 3.86, 5.90 and 4.64 GB
-    # Reported as null: the kernels gained the t-hop weight of the anisotropic operator
-    # (a kernel parameter, no memory access changed) after that capture, and the
-    # counters were not taken again; the captured value stays in traffic_last_capture.
-    traffic = None
-    traffic_last = TRAFFIC_F32_32C64_12RHS if (dims == DIMS and args.sloppy == "f32") else None
+    # DRAM bytes per launch of the dominant kernel: the per-(site, RHS) traffic measured on
+    # the small case (same kernel variant, same launch mix) times the units of one launch
+    # here (sites per parity x 12); only for the FP32 inner solver it was measured for
+    units = dims[0] * dims[1] * dims[2] * dims[3] // 2 * 12
+    traffic = TRAFFIC_F32_12RHS_PER_SITE_RHS * units if args.sloppy == "f32" else None
     value = replicas_value(ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -372,12 +410,22 @@ def run_ours(args, rank, world, local):
                    "l2": "working set >> L2 (no flush needed)"},
         "solve": {"seconds": ms / 1e3, "iters_per_rhs": iters, "worst_true_residual": worst,
                   "reliable_updates": statistics.mean(i["reliable_updates"] for i in infos)},
+        "plain_f32_single_rhs": {"seconds": plain_ms / 1e3, "runs": len(p_runs),
+                                 "iters_per_rhs": statistics.mean(i["iters"] for i in p_infos),
+                                 "worst_true_residual": max(i["true_residual"] for i in p_infos),
+                                 "speedup_of_this_solve": plain_ms / ms,
+                                 "method": "12 sequential wcl_invert calls with nrhs 1: FP32 BiCGStab restarted "
+                                           "from the IEEE FP64 true residual at each 1e-5 reduction, same GPU, "
+                                           "same workload, CUDA events"},
         "roofline": {"bound": "hbm", "kernel": f"{args.sloppy} 12-RHS fused dslash+clover (inner solver, tuned variant)",
                      "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": (gbs / peak) if gbs else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": s_bytes / max(1, s_n), "launches_timed": s_n,
                      "avg_launch_ms": s_ms / max(1, s_n),
-                     "traffic": traffic, "traffic_last_capture": traffic_last,
+                     "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of 8 launches of this "
+                                       "kernel in the same solve on 32^3x16 (361.7 B per site-RHS against 320 "
+                                       "algorithmic, 1.13x), scaled by the site-RHS of one launch here",
                      "gflops": s_flops / (s_ms * 1e-3) / 1e9 if s_ms > 0 else None,
                      "share_of_profiled_solve": s_ms / max(1e-9, pinfos[0]["seconds"] * 1e3)},
         "fp64_dslash": {"bound": "alu", "kernel": "FP64 12-RHS fused dslash (final residual replacements)",
@@ -396,6 +444,12 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(iters)
+        # the oracle's own FP64 true residual of every right-hand side of the benchmark's
+        # solve, over the whole lattice (slab by slab, spawned processes), and its time
+        rec = oracle_true_residuals(gauge, x.cpu().numpy(), src, dims)
+        line["cpu_baseline"]["true_residual_recompute"] = rec
+        line["solve"]["worst_true_residual_oracle"] = rec["worst"]
+    del gauge
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
