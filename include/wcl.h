@@ -87,7 +87,11 @@ typedef enum {
   WCL_BICGSTAB = 0,      /* BiCGStab on M_hat (Sec. II.E: default for clover) */
   WCL_CGNR = 1,          /* CG on M_hat^+ M_hat (Sec. II.E: CG) */
   WCL_FGCR_LEARNED = 2,  /* flexible GCR on M_hat with the learned preconditioner */
-  WCL_GCR = 3            /* the same GCR without a preconditioner (the comparison method) */
+  WCL_GCR = 3,           /* the same GCR without a preconditioner (the comparison method) */
+  WCL_FGCR_MG = 4        /* flexible GCR on the whole-lattice M preconditioned by the two-level
+                            multigrid K-cycle of wcl_mg_setup (Sec. II.E: QUDA's multigrid), FP32
+                            between IEEE FP64 true-residual restarts; right-hand sides one after
+                            another, wcl_invert only.  Uses tol, maxiter and gcr_nkrylov. */
 } wcl_solver;
 
 typedef struct {
@@ -393,6 +397,64 @@ wcl_status wcl_get_stats(wcl_ctx* ctx, wcl_stats* out, int reset);
  *   complex128, caller-owned; anything else (page-locked or pageable host memory,
  *   another GPU's memory) is WCL_ERR_INVALID_ARG. */
 wcl_status wcl_apply_Mpc_noalloc(wcl_ctx* ctx, void* d_out_e, const void* d_in_e, int dagger);
+
+/* ---- adaptive aggregation multigrid (Sec. II.E; Sec. III.B passes one block size per level) ----
+ * Two levels on the whole-lattice operator M.  The paper names the method without its
+ * steps; the library takes the standard aggregation ones:
+ *   null space : nvec start vectors relaxed towards M x = 0 by relax_steps minimal-residual
+ *                steps (r = -M x; alpha = <M r, r> / |M r|^2; x += alpha r; r -= alpha M r),
+ *                then normalised;
+ *   P          : per block of block[0] x block[1] x block[2] x block[3] sites and per
+ *                chirality (spins {0,1} and {2,3}) the restrictions of the null vectors,
+ *                made orthonormal (modified Gram-Schmidt, twice): P^+ P = 1;
+ *   coarse op  : A_c = P^+ M P as the nine-point stencil
+ *                (A_c c)(x) = X(x) c(x) + sum_mu [Yf_mu(x) c(x + mu) + Yb_mu(x) c(x - mu)]
+ *                of (2 nvec) x (2 nvec) blocks, built from the links, the clover term and P;
+ *   K-cycle    : pre minimal-residual steps from zero, e += P A_c^-1 P^+ (r - M e) with
+ *                the coarse system solved by GCR(coarse_nkrylov) to coarse_tol (at most
+ *                coarse_maxiter steps), post minimal-residual steps.
+ * Arithmetic is FP32 (FP64 sums).  Coarse vectors are [Ct][Cz][Cy][Cx][2][nvec] complex128,
+ * C_mu = L_mu / block[mu], chirality before vector index. */
+typedef struct {
+  int block[4];        /* block extents (x, y, z, t); each divides the lattice extent */
+  int nvec;            /* null vectors, 1..32 and at most 6 x block sites */
+  int relax_steps;     /* minimal-residual steps per null vector (0: the starts as given) */
+  int pre, post;       /* smoothing steps of the K-cycle */
+  double coarse_tol;   /* relative residual of the coarse GCR */
+  int coarse_maxiter;  /* coarse GCR steps at most */
+  int coarse_nkrylov;  /* coarse GCR restart length (1..64) */
+} wcl_mg_params;
+
+/* Defaults: blocks 4^4, 24 vectors, 20 relaxation steps, 2 + 2 smoothing steps,
+ * coarse GCR(8) to 0.1 in at most 50 steps. */
+void wcl_default_mg_params(wcl_mg_params* p);
+
+/* Build the hierarchy of ctx's operator (after wcl_load_gauge) from nvec start vectors
+ * d_starts: [nvec][QDP fermion] complex128, device or page-locked host (random numbers
+ * are the caller's).  WCL_ERR_BREAKDOWN if a vector vanishes or the vectors are linearly
+ * dependent on a block. */
+wcl_status wcl_mg_setup(wcl_ctx* ctx, const void* d_starts, const wcl_mg_params* params);
+
+/* d_out = K-cycle(d_in): one application of the preconditioner to a whole-lattice field
+ * (QDP fermion, complex128); coarse_iters (may be NULL) receives the coarse GCR steps. */
+wcl_status wcl_mg_cycle(wcl_ctx* ctx, void* d_out, const void* d_in, int* coarse_iters);
+
+/* Restriction P^+ (QDP fermion -> coarse vector) and prolongation P (coarse -> QDP
+ * fermion, overwritten); coarse vectors are complex128, device or host memory. */
+wcl_status wcl_mg_restrict(wcl_ctx* ctx, void* d_coarse, const void* d_fine);
+wcl_status wcl_mg_prolong(wcl_ctx* ctx, void* d_fine, const void* d_coarse);
+
+/* d_out = A_c d_in on coarse vectors (complex128, device or host). */
+wcl_status wcl_mg_coarse_apply(wcl_ctx* ctx, void* d_out, const void* d_in);
+
+/* Copy P to the host: [2][Lt][Lz][Ly][Lx/2] sites (QDP order) x [12] rows (3 spin + colour)
+ * x [2 nvec] columns (chirality nvec + vector), complex128 interleaved; entries whose row
+ * and column chiralities differ are zero. */
+wcl_status wcl_mg_get_prolongator(wcl_ctx* ctx, double* h_P);
+
+/* Copy the stencil to the host: [9][coarse site][2 nvec][2 nvec] complex128 (row, column),
+ * block 0 = X, 1 + 2 mu = Yf_mu, 2 + 2 mu = Yb_mu. */
+wcl_status wcl_mg_get_stencil(wcl_ctx* ctx, double* h_Y);
 
 /* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */
 wcl_status wcl_destroy(wcl_ctx* ctx);

@@ -11,6 +11,7 @@ from .wcl import (  # noqa: F401
     wcl_default_params,
     ptc_flatten,
     ptc_unflatten,
+    wcl_default_mg_params,
     wcl_default_train_params,
     wcl_gamma,
     wcl_invert_batch,

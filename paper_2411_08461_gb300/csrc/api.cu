@@ -400,7 +400,8 @@ static wcl_status check_params(const wcl_solve_params* p) {
     set_error("invalid solve parameters (outer F64 or DF64, 0 < delta < 1, tol > 0)");
     return WCL_ERR_INVALID_ARG;
   }
-  if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED && p->solver != WCL_GCR) {
+  if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED && p->solver != WCL_GCR &&
+      p->solver != WCL_FGCR_MG) {
     set_error("unknown solver %d", (int)p->solver);
     return WCL_ERR_INVALID_ARG;
   }
@@ -436,6 +437,20 @@ wcl_status wcl_invert(wcl_ctx* c, void* d_x, const void* d_b, int nrhs, const wc
   if (!field_ptr(c, d_x, &d_x, "wcl_invert x") || !field_ptr(c, d_b, &d_b, "wcl_invert b"))
     return WCL_ERR_INVALID_ARG;
   WCL_CHECK(enter(c));
+  if (params->solver == WCL_FGCR_MG) {
+    // one right-hand side after the other through the multigrid-preconditioned FGCR
+    const auto t0 = std::chrono::steady_clock::now();
+    wcl_status worst = WCL_OK;
+    for (int k = 0; k < nrhs && worst != WCL_ERR_NO_PRECOND; k++) {
+      wcl_status s = mg_solve_one(c, d_b, d_x, (long)k * 2 * c->lat.vh * 12, *params, &info[k]);
+      if (s != WCL_OK) return leave(c, s);
+      if (worst == WCL_OK && info[k].status != WCL_OK) worst = (wcl_status)info[k].status;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < nrhs; k++) info[k].seconds = secs;
+    if (worst != WCL_OK) set_error("right-hand side did not reach the tolerance (multigrid FGCR)");
+    return leave(c, worst);
+  }
   std::vector<wcl_ctx*> v{c};
   void* xs[1] = {d_x};
   const void* bs[1] = {d_b};
@@ -450,6 +465,10 @@ wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, co
     return WCL_ERR_INVALID_ARG;
   }
   WCL_CHECK(check_params(params));
+  if (params->solver == WCL_FGCR_MG) {
+    set_error("wcl_invert_batch: the multigrid solver runs through wcl_invert, one lattice at a time");
+    return WCL_ERR_INVALID_ARG;
+  }
   std::vector<wcl_ctx*> v;
   for (int i = 0; i < nctx; i++) {
     if (!ctxs[i] || !d_x[i] || !d_b[i]) {
@@ -547,6 +566,7 @@ wcl_status wcl_destroy(wcl_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_lattice(c);
   ptc_free(c);
+  mg_free(c);
   for (auto& kv : c->ws) cudaFree(kv.second.p);
   for (auto& kv : c->hws) cudaFreeHost(kv.second.p);
   for (auto& t : c->ev_pool) {

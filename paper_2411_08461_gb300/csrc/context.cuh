@@ -65,6 +65,7 @@ struct wcl_ctx {
   bool paired_rhs = false;       // untuned multi-RHS FP32/16-bit dslash: the packed-pair kernel
   bool prefetch_spinors = false; // untuned multi-RHS dslash: next hop's spinor prefetched in registers
   int blas_block = 256;
+  void* mg = nullptr;  // multigrid hierarchy (mg.cu), built by wcl_mg_setup
 };
 
 namespace wcl {
@@ -204,5 +205,10 @@ wcl_status hws_get(wcl_ctx* c, const std::string& name, size_t bytes, void** out
 wcl_status noalloc_prepare(int device);
 // load the module of the FP64 per-thread dslash kernels (dslash_f64.cu) without a launch
 cudaError_t load_dslash_f64_module();
+// multigrid (mg.cu): release the hierarchy; solve M x = b for right-hand side at complex
+// offset rhs_off_c of the caller's QDP buffers by FGCR preconditioned with the K-cycle
+void mg_free(wcl_ctx* c);
+wcl_status mg_solve_one(wcl_ctx* c, const void* d_b, void* d_x, long rhs_off_c, const wcl_solve_params& prm,
+                        wcl_solve_info* info);
 
 }  // namespace wcl

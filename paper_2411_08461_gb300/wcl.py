@@ -21,7 +21,7 @@ STATUS_NAMES = {
     9: "WCL_ERR_NO_GAUGE", 10: "WCL_ERR_NO_PRECOND",
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
-SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3}
+SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3, "fgcr_mg": 4}
 PTC_NWEIGHTS = 5760
 WCL_OPT_TENSOR_CORES = 1
 WCL_OPT_SHARED_LINKS = 2
@@ -46,6 +46,14 @@ class wcl_solve_info(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int), ("true_residual", ctypes.c_double), ("reliable_updates", ctypes.c_int),
         ("status", ctypes.c_int), ("seconds", ctypes.c_double),
+    ]
+
+
+class wcl_mg_params(ctypes.Structure):
+    _fields_ = [
+        ("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("relax_steps", ctypes.c_int), ("pre", ctypes.c_int),
+        ("post", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("coarse_maxiter", ctypes.c_int),
+        ("coarse_nkrylov", ctypes.c_int),
     ]
 
 
@@ -109,6 +117,14 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_double)]),
     "wcl_contract": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
+    "wcl_default_mg_params": (None, [ctypes.POINTER(wcl_mg_params)]),
+    "wcl_mg_setup": (ctypes.c_int, [_P, _P, ctypes.POINTER(wcl_mg_params)]),
+    "wcl_mg_cycle": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "wcl_mg_restrict": (ctypes.c_int, [_P, _P, _P]),
+    "wcl_mg_prolong": (ctypes.c_int, [_P, _P, _P]),
+    "wcl_mg_coarse_apply": (ctypes.c_int, [_P, _P, _P]),
+    "wcl_mg_get_prolongator": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "wcl_mg_get_stencil": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -273,6 +289,80 @@ class Context:
                                                     _ptr(in_e, torch.complex128, n, "in_e"), int(dagger)),
                "wcl_apply_Mpc_noalloc")
 
+    # ---- multigrid ---------------------------------------------------------------
+    def _mg_coarse_numel(self):
+        p = self._mg_params
+        cs = 1
+        for d in range(4):
+            cs *= self.dims[d] // p.block[d]
+        return cs * 2 * p.nvec
+
+    def wcl_mg_setup(self, starts, params: wcl_mg_params | None = None):
+        """Build the two-level hierarchy from `nvec` start vectors ([nvec][QDP fermion] complex128)."""
+        import torch
+
+        params = params or wcl_default_mg_params()
+        _check(load_library().wcl_mg_setup(self.handle, _ptr(starts, torch.complex128,
+                                                             self.fermion_numel * params.nvec, "starts", True),
+                                           ctypes.byref(params)), "wcl_mg_setup")
+        self._mg_params = params
+
+    def wcl_mg_cycle(self, out, inp) -> int:
+        import torch
+
+        it = ctypes.c_int(0)
+        _check(load_library().wcl_mg_cycle(self.handle, _ptr(out, torch.complex128, self.fermion_numel, "out", True),
+                                           _ptr(inp, torch.complex128, self.fermion_numel, "in", True),
+                                           ctypes.byref(it)), "wcl_mg_cycle")
+        return it.value
+
+    def wcl_mg_restrict(self, coarse, fine):
+        import torch
+
+        _check(load_library().wcl_mg_restrict(self.handle, _ptr(coarse, torch.complex128, self._mg_coarse_numel(),
+                                                                "coarse"),
+                                              _ptr(fine, torch.complex128, self.fermion_numel, "fine", True)),
+               "wcl_mg_restrict")
+
+    def wcl_mg_prolong(self, fine, coarse):
+        import torch
+
+        _check(load_library().wcl_mg_prolong(self.handle, _ptr(fine, torch.complex128, self.fermion_numel, "fine", True),
+                                             _ptr(coarse, torch.complex128, self._mg_coarse_numel(), "coarse")),
+               "wcl_mg_prolong")
+
+    def wcl_mg_coarse_apply(self, out, inp):
+        import torch
+
+        n = self._mg_coarse_numel()
+        _check(load_library().wcl_mg_coarse_apply(self.handle, _ptr(out, torch.complex128, n, "out"),
+                                                  _ptr(inp, torch.complex128, n, "in")), "wcl_mg_coarse_apply")
+
+    def wcl_mg_get_prolongator(self):
+        """P as a numpy array [2][Lt][Lz][Ly][Lx/2][12][2 nvec] complex128 (QDP site order)."""
+        import numpy as np
+
+        lx, ly, lz, lt = self.dims
+        n = 2 * self._mg_params.nvec
+        buf = np.zeros(self.volume * 12 * n * 2, dtype=np.float64)
+        _check(load_library().wcl_mg_get_prolongator(self.handle, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_mg_get_prolongator")
+        return buf.view(np.complex128).reshape(2, lt, lz, ly, lx // 2, 12, n)
+
+    def wcl_mg_get_stencil(self):
+        """(X, Yf, Yb) as numpy arrays (Ct, Cz, Cy, Cx, n, n) and (4, Ct, Cz, Cy, Cx, n, n), n = 2 nvec."""
+        import numpy as np
+
+        p = self._mg_params
+        cd = [self.dims[d] // p.block[d] for d in range(4)]
+        nc = cd[0] * cd[1] * cd[2] * cd[3]
+        n = 2 * p.nvec
+        buf = np.zeros(9 * nc * n * n * 2, dtype=np.float64)
+        _check(load_library().wcl_mg_get_stencil(self.handle, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "wcl_mg_get_stencil")
+        y = buf.view(np.complex128).reshape(9, cd[3], cd[2], cd[1], cd[0], n, n)
+        return y[0], np.stack([y[1 + 2 * mu] for mu in range(4)]), np.stack([y[2 + 2 * mu] for mu in range(4)])
+
     def wcl_invert(self, x, b, nrhs: int = 1, params: wcl_solve_params | None = None, check: bool = True):
         import torch
 
@@ -421,6 +511,17 @@ def wcl_default_train_params(**overrides) -> wcl_train_params:
     load_library().wcl_default_train_params(ctypes.byref(p))
     for k, v in overrides.items():
         setattr(p, k, v)
+    return p
+
+
+def wcl_default_mg_params(**overrides) -> wcl_mg_params:
+    p = wcl_mg_params()
+    load_library().wcl_default_mg_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "block":
+            p.block = (ctypes.c_int * 4)(*v)
+        else:
+            setattr(p, k, v)
     return p
 
 
