@@ -64,13 +64,18 @@ def parse():
     ap.add_argument("--pairs", type=int, default=2000, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator"],
+                    choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator", "mg"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures); "
                          "batch: four uneven lattices x 12 Z2 sources in one batched solve vs single-RHS "
                          "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve; "
                          "propagator: the Sec. III.B sequence (wall propagators, sequential propagator, "
-                         "two- and three-point functions) on --dims, with the contraction kernel's roofline")
-    ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of --case propagator")
+                         "two- and three-point functions) on --dims, with the contraction kernel's roofline; "
+                         "mg: the two-level multigrid (setup, then FGCR-MG on the 12 point sources) against "
+                         "the batched BiCGStab solve on --dims at --kappa")
+    ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of --case propagator / mg")
+    ap.add_argument("--kappa", type=float, default=KAPPA, help="hopping parameter of --case mg")
+    ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
+    ap.add_argument("--mg-nvec", type=int, default=24, help="--case mg: null vectors")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
     ap.add_argument("--dims", default="32,32,32,64", help="lattice of --case solve (the bench line uses 32^3x64)")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
@@ -864,6 +869,63 @@ def run_compare_case(args):
     return 0
 
 
+def run_mg_case(args):
+    """Two-level multigrid on --dims at --kappa: the hierarchy's setup (null-space relaxation,
+    prolongator, coarse stencil) timed, then FGCR preconditioned by the K-cycle on the 12
+    spin-colour point sources to --tol, against the batched 12-RHS BiCGStab solve of the
+    bench line on the same field (CUDA events on the library's stream)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dims = tuple(int(v) for v in args.dims.split(","))
+    block = tuple(int(v) for v in args.mg_block.split(","))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pkg.Context(dims, stream=stream)
+    ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, SEED)).to(dev), args.kappa, CSW)
+    src = torch.from_numpy(np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])).to(dev)
+    x = torch.zeros_like(src)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    starts = torch.from_numpy(W.gaussian_fermion(dims, 500, nrhs=args.mg_nvec)).to(dev)
+    mprm = pkg.wcl_default_mg_params(block=block, nvec=args.mg_nvec)
+    ctx.wcl_mg_setup(starts, mprm)  # warm-up (tuner, module loading)
+    setup_s, _ = timed(lambda: ctx.wcl_mg_setup(starts, mprm))
+    del starts
+    mg = pkg.wcl_default_params(solver="fgcr_mg", tol=args.tol, gcr_nkrylov=20)
+    ctx.wcl_invert(x[:1], src[:1], 1, mg)  # warm-up
+    mg_s, infos = timed(lambda: ctx.wcl_invert(x, src, 12, mg)[1])
+    bi = pkg.wcl_default_params(solver="bicgstab", sloppy="f32", tol=args.tol, check_every=2, delta_reliable=3e-4)
+    ctx.wcl_invert(x, src, 12, bi)
+    bi_s, binfos = timed(lambda: ctx.wcl_invert(x, src, 12, bi)[1])
+    print(json.dumps({"case": "mg", "lattice": dims, "kappa": args.kappa, "block": block, "nvec": args.mg_nvec,
+                      "relax_steps": mprm.relax_steps, "setup_seconds": setup_s,
+                      "mg_fgcr": {"seconds": mg_s, "outer_iters_per_rhs": float(np.mean([i["iters"] for i in infos])),
+                                  "restarts_per_rhs": float(np.mean([i["reliable_updates"] for i in infos])),
+                                  "worst_true_residual": max(i["true_residual"] for i in infos)},
+                      "batched_bicgstab_f32": {"seconds": bi_s,
+                                               "iters_per_rhs": float(np.mean([i["iters"] for i in binfos])),
+                                               "worst_true_residual": max(i["true_residual"] for i in binfos)},
+                      "mg_over_bicgstab_time": (mg_s + setup_s) / bi_s}))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.case == "mhat":
@@ -878,6 +940,8 @@ def main():
         return run_precond_case(args)
     if args.case == "propagator":
         return run_propagator_case(args)
+    if args.case == "mg":
+        return run_mg_case(args)
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores only; other ranks exit without work
         return run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
