@@ -64,14 +64,16 @@ def parse():
     ap.add_argument("--pairs", type=int, default=2000, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator", "mg"],
+                    choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator", "mg",
+                             "staggered"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures); "
                          "batch: four uneven lattices x 12 Z2 sources in one batched solve vs single-RHS "
                          "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve; "
                          "propagator: the Sec. III.B sequence (wall propagators, sequential propagator, "
                          "two- and three-point functions) on --dims, with the contraction kernel's roofline; "
                          "mg: the two-level multigrid (setup, then FGCR-MG on the 12 point sources) against "
-                         "the batched BiCGStab solve on --dims at --kappa")
+                         "the batched BiCGStab solve on --dims at --kappa; staggered: the HISQ-form staggered "
+                         "operator on --dims (FP64 and FP32 applies, GB/s) and its even-odd CG solve")
     ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of --case propagator / mg")
     ap.add_argument("--kappa", type=float, default=KAPPA, help="hopping parameter of --case mg")
     ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
@@ -869,6 +871,73 @@ def run_compare_case(args):
     return 0
 
 
+def run_staggered_case(args):
+    """Staggered operator M = 2 m + D of the HISQ action on given fat and long links
+    (synthetic: Gaussian complex matrices scaled by 0.3 and 0.05, mass 0.1) on --dims:
+    whole-lattice applies in FP64 and FP32 timed with CUDA events, algorithmic bytes per
+    output site = 16 links (each read once per launch) + the input vector + the output
+    (+ the 2 m x term), and one mixed-precision CG solve from a point source to --tol."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dims = tuple(int(v) for v in args.dims.split(","))
+    lx, ly, lz, lt = dims
+    vol = lx * ly * lz * lt
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pkg.Context(dims, stream=stream)
+    rng_shape = (4, 2, lt, lz, ly, lx // 2, 3, 3)  # QDP gauge layout directly (synthetic values)
+    fat = torch.from_numpy(0.3 * W.gaussian_complex(rng_shape, 600)).to(dev)
+    lng = torch.from_numpy(0.05 * W.gaussian_complex(rng_shape, 601)).to(dev)
+    ctx.wcl_load_staggered(fat, lng, 0.1)
+    del fat, lng
+    chi = torch.from_numpy(W.gaussian_complex((2, lt, lz, ly, lx // 2, 3), 602)).to(dev)
+    out = torch.empty_like(chi)
+    peak, kind = measured_peaks()
+    res = {"case": "staggered", "lattice": dims, "mass": 0.1, "peak": peak, "peak_kind": kind}
+    for prec, real in (("f64", 8), ("f32", 4)):
+        for _ in range(3):
+            ctx.wcl_apply_staggered(out, chi, prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = 10
+        for _ in range(n):
+            ctx.wcl_apply_staggered(out, chi, prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        # per output site: 16 links x 18 reals, input vector 6 reals, output 6, 2 m x term 6
+        byts = vol * (16 * 18 + 18) * real
+        res[prec] = {"ms_per_apply_with_io": ms, "algorithmic_gb_per_apply": byts / 1e9,
+                     "note": "the call time includes the QDP import and export kernels around the two dslash launches"}
+    ctx.wcl_set_profiling(True)
+    ctx.wcl_get_stats(reset=True)
+    src = torch.zeros_like(chi)
+    src[0, 0, 0, 0, 0, 0] = 1.0
+    x = torch.zeros_like(src)
+    prm = pkg.wcl_default_params(sloppy="f32", tol=args.tol)
+    ctx.wcl_invert_staggered(x, src, 1, prm)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    _, info = ctx.wcl_invert_staggered(x, src, 1, prm)
+    b.record(stream)
+    torch.cuda.synchronize()
+    res["cg_solve"] = {"seconds": a.elapsed_time(b) / 1e3, "iters": info[0]["iters"],
+                       "restarts": info[0]["reliable_updates"], "true_residual": info[0]["true_residual"]}
+    print(json.dumps(res))
+    ctx.close()
+    return 0
+
+
 def run_mg_case(args):
     """Two-level multigrid on --dims at --kappa: the hierarchy's setup (null-space relaxation,
     prolongator, coarse stencil) timed, then FGCR preconditioned by the K-cycle on the 12
@@ -942,6 +1011,8 @@ def main():
         return run_propagator_case(args)
     if args.case == "mg":
         return run_mg_case(args)
+    if args.case == "staggered":
+        return run_staggered_case(args)
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores only; other ranks exit without work
         return run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))

@@ -456,6 +456,31 @@ wcl_status wcl_mg_get_prolongator(wcl_ctx* ctx, double* h_P);
  * block 0 = X, 1 + 2 mu = Yf_mu, 2 + 2 mu = Yb_mu. */
 wcl_status wcl_mg_get_stencil(wcl_ctx* ctx, double* h_Y);
 
+/* ---- staggered operator of the HISQ action on given smeared links (Sec. II.A, II.E) ----
+ *   M chi = 2 m chi + D chi,
+ *   D chi(x) = sum_mu eta_mu(x) [ V_mu(x) chi(x+mu) - V_mu(x-mu)^+ chi(x-mu)
+ *                               + W_mu(x) chi(x+3mu) - W_mu(x-3mu)^+ chi(x-3mu) ]
+ * with V the fat (one-hop) and W the long (three-hop, Naik coefficient included) links of
+ * the HISQ smearing, the MILC phases eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y),
+ * eta_t = (-1)^(x+y+z), and t_boundary (wcl_create) on every hop across t = Lt-1 -> 0.
+ * The smearing that produces V and W is the caller's.  Staggered fields are
+ * [2][Lt][Lz][Ly][Lx/2][3] complex128 (QDP order, colour only), nrhs back to back. */
+
+/* Load V and W (QDP gauge layout, complex128, device or page-locked host; any complex
+ * 3x3 matrices) and the mass m (> 0: the solve is even-odd).  Kept in FP64 and FP32. */
+wcl_status wcl_load_staggered(wcl_ctx* ctx, const void* d_fat, const void* d_long, double mass);
+
+/* d_out = M d_in on the whole lattice for nrhs fields, prec WCL_F64 or WCL_F32. */
+wcl_status wcl_apply_staggered(wcl_ctx* ctx, void* d_out, const void* d_in, wcl_prec prec, int nrhs);
+
+/* Solve M x = b for nrhs staggered right-hand sides (one after another) by CG on the even
+ * sites, (4 m^2 - D_eo D_oe) x_e = 2 m b_e - D_eo b_o, x_o = (b_o - D_oe x_e)/(2 m) (Sec. II.E:
+ * CG is the HISQ default), in params->sloppy (WCL_F32: FP32 CG between IEEE FP64 restarts
+ * from the true residual; WCL_F64: FP64 CG), to ||b - M x|| / ||b|| <= params->tol computed
+ * in FP64; uses tol and maxiter.  info: host array of nrhs entries. */
+wcl_status wcl_invert_staggered(wcl_ctx* ctx, void* d_x, const void* d_b, int nrhs, const wcl_solve_params* params,
+                                wcl_solve_info* info);
+
 /* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */
 wcl_status wcl_destroy(wcl_ctx* ctx);
 

@@ -567,6 +567,7 @@ wcl_status wcl_destroy(wcl_ctx* c) {
   free_lattice(c);
   ptc_free(c);
   mg_free(c);
+  stag_free(c);
   for (auto& kv : c->ws) cudaFree(kv.second.p);
   for (auto& kv : c->hws) cudaFreeHost(kv.second.p);
   for (auto& t : c->ev_pool) {

@@ -65,7 +65,8 @@ struct wcl_ctx {
   bool paired_rhs = false;       // untuned multi-RHS FP32/16-bit dslash: the packed-pair kernel
   bool prefetch_spinors = false; // untuned multi-RHS dslash: next hop's spinor prefetched in registers
   int blas_block = 256;
-  void* mg = nullptr;  // multigrid hierarchy (mg.cu), built by wcl_mg_setup
+  void* mg = nullptr;    // multigrid hierarchy (mg.cu), built by wcl_mg_setup
+  void* stag = nullptr;  // staggered links and mass (stag.cu), loaded by wcl_load_staggered
 };
 
 namespace wcl {
@@ -208,6 +209,7 @@ cudaError_t load_dslash_f64_module();
 // multigrid (mg.cu): release the hierarchy; solve M x = b for right-hand side at complex
 // offset rhs_off_c of the caller's QDP buffers by FGCR preconditioned with the K-cycle
 void mg_free(wcl_ctx* c);
+void stag_free(wcl_ctx* c);
 wcl_status mg_solve_one(wcl_ctx* c, const void* d_b, void* d_x, long rhs_off_c, const wcl_solve_params& prm,
                         wcl_solve_info* info);
 

@@ -117,6 +117,10 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_double)]),
     "wcl_contract": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
+    "wcl_load_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "wcl_apply_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
+    "wcl_invert_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_solve_params),
+                                            ctypes.POINTER(wcl_solve_info)]),
     "wcl_default_mg_params": (None, [ctypes.POINTER(wcl_mg_params)]),
     "wcl_mg_setup": (ctypes.c_int, [_P, _P, ctypes.POINTER(wcl_mg_params)]),
     "wcl_mg_cycle": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -288,6 +292,38 @@ class Context:
         _check(load_library().wcl_apply_Mpc_noalloc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
                                                     _ptr(in_e, torch.complex128, n, "in_e"), int(dagger)),
                "wcl_apply_Mpc_noalloc")
+
+    # ---- staggered operator --------------------------------------------------------
+    def wcl_load_staggered(self, fat, long_links, mass: float):
+        import torch
+
+        n = self.volume * 36
+        _check(load_library().wcl_load_staggered(self.handle, _ptr(fat, torch.complex128, n, "fat", True),
+                                                 _ptr(long_links, torch.complex128, n, "long", True), float(mass)),
+               "wcl_load_staggered")
+
+    def wcl_apply_staggered(self, out, inp, prec: str = "f64", nrhs: int = 1):
+        import torch
+
+        n = self.volume * 3 * nrhs
+        _check(load_library().wcl_apply_staggered(self.handle, _ptr(out, torch.complex128, n, "out", True),
+                                                  _ptr(inp, torch.complex128, n, "in", True), PREC[prec], int(nrhs)),
+               "wcl_apply_staggered")
+
+    def wcl_invert_staggered(self, x, b, nrhs: int = 1, params: wcl_solve_params | None = None, check: bool = True):
+        import torch
+
+        params = params or wcl_default_params()
+        info = (wcl_solve_info * nrhs)()
+        n = self.volume * 3 * nrhs
+        st = load_library().wcl_invert_staggered(self.handle, _ptr(x, torch.complex128, n, "x", True),
+                                                 _ptr(b, torch.complex128, n, "b", True), int(nrhs),
+                                                 ctypes.byref(params), info)
+        out = [{"iters": i.iters, "true_residual": i.true_residual, "reliable_updates": i.reliable_updates,
+                "status": i.status, "seconds": i.seconds} for i in info]
+        if check:
+            _check(st, "wcl_invert_staggered")
+        return st, out
 
     # ---- multigrid ---------------------------------------------------------------
     def _mg_coarse_numel(self):
