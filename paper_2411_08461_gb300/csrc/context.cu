@@ -175,6 +175,8 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   }
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
+  if (ch.variant == V_TMA) return prec == F32 ? launch_dslash_tma(a, dagger, mode, st, ctxs[0]->d_flags)
+                                               : cudaErrorInvalidValue;
   if (ch.variant == V_PAIR || ch.variant == V_PAIR_ZB) {
     switch (prec) {
       case F32: return launch_dslash_pair<F32>(a, dagger, mode, ts, st);
@@ -208,9 +210,18 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   const bool tc_ok = use_tc(c0, prec, nrhs, mode);
   const bool mr_ok = use_mrhs(c0, prec, nrhs, mode);
   const bool pair_ok = use_pair(c0, prec, nrhs, mode);
+  bool tma_ok = mr_ok && prec == F32 && nlat == 1;
+  if (tma_ok) {
+    LatGeom gg{};
+    gg.lxh = c0->lat.dims[0] / 2;
+    gg.vh = (int)c0->lat.vh;
+    tma_ok = tma_eligible(gg, nrhs);
+  }
   TuneChoice dflt{V_THREAD, c0->dslash_block[prec == DF64 ? F64 : prec]};
   if (tc_ok)
     dflt = {V_TC, tc_tile_sites()};
+  else if (tma_ok && c0->tma_staging)
+    dflt = {V_TMA, 16};
   else if (pair_ok && c0->paired_rhs)
     dflt = c0->blocked_tiles ? TuneChoice{V_PAIR_ZB, 16} : TuneChoice{V_PAIR, c0->shared_links};
   else if (mr_ok && c0->staged_spinors && prec != F64)
@@ -224,7 +235,8 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   std::string key = "dslash p" + std::to_string(prec) + " m" + std::to_string(mode) + " d" + std::to_string(dagger) +
                     " n" + std::to_string(nrhs) + " o" + std::to_string((int)tc_ok) + std::to_string((int)mr_ok) +
                     std::to_string((int)c0->staged_spinors) + std::to_string((int)c0->blocked_tiles) +
-                    std::to_string((int)c0->paired_rhs) + std::to_string((int)c0->prefetch_spinors);
+                    std::to_string((int)c0->paired_rhs) + std::to_string((int)c0->prefetch_spinors) +
+                    std::to_string((int)c0->tma_staging);
   for (auto* c : ctxs)
     key += " " + std::to_string(c->lat.dims[0]) + "x" + std::to_string(c->lat.dims[1]) + "x" +
            std::to_string(c->lat.dims[2]) + "x" + std::to_string(c->lat.dims[3]);
@@ -257,6 +269,7 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
     }
     if (zb) cand.push_back({V_SMEM_ZB, 16});
     if (zb && prec != F64) cand.push_back({V_SMEM_PF_ZB, 16});
+    if (tma_ok) cand.push_back({V_TMA, 16});
     if (pair_ok) {
       for (int ts : {8, 16, 32}) cand.push_back({V_PAIR, ts});
       if (zb) cand.push_back({V_PAIR_ZB, 16});

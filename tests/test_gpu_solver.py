@@ -108,6 +108,29 @@ def test_batch_of_lattices_four_rhs(pkg, solver, shared_links):
     _batch_solve(pkg, solver, shared_links, nrhs=4, sloppy="f32")
 
 
+@pytest.mark.parametrize("solver", ["bicgstab", "cgnr"])
+def test_tma_staged_kernel_in_a_solve(pkg, solver):
+    """The TMA-staged kernel with its fused reductions inside BiCGStab and CGNR on a lattice
+    with Lx = 32, every true residual recomputed by the oracle."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_AUTOTUNE, WCL_OPT_TMA_STAGING
+
+    dims = (32, 4, 4, 6)
+    g = W.gauge_links(dims, 0.3, 37)
+    c = pkg.Context(dims)
+    c.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
+    c.wcl_set_option(WCL_OPT_TMA_STAGING, 1)
+    c.wcl_load_gauge(cuda(g), 0.1235, 1.0)
+    op = dirac.from_qdp_problem(g, dims, 0.1235, 1.0)
+    b = W.z2_fermion(dims, 38, nrhs=5)
+    b[2] *= 1e3
+    x = cuda(np.zeros_like(b))
+    _, info = c.wcl_invert(x, cuda(b), 5, pkg.wcl_default_params(solver=solver, sloppy="f32", tol=1e-10))
+    xh = host(x)
+    for r in range(5):
+        assert _oracle_true_residual(op, xh[r], b[r]) <= 1e-10, (r, info)
+    c.close()
+
+
 @pytest.mark.parametrize("sloppy", ["f32", "bf16", "f16"])
 def test_batch_of_lattices_paired_odd_rhs(pkg, sloppy):
     """Five RHS through the packed-pair kernel (the last pair holds one right-hand side) with
