@@ -91,7 +91,10 @@ def parse():
     ap.add_argument("--paired-rhs", type=int, default=0,
                     help="--case mhat: packed-pair multi-RHS kernel (two RHS per thread, FFMA2) when the tuner is off")
     ap.add_argument("--blocked-tiles", type=int, default=0, help="--case mhat: z-blocked tile order (tuner off)")
-    ap.add_argument("--tma-staging", type=int, default=0, help="--case mhat: TMA-staged persistent kernel (tuner off)")
+    ap.add_argument("--tma-staging", type=int, default=0,
+                    help="--case mhat: TMA-staged kernel, 1 persistent / 2 one CTA per tile (tuner off)")
+    ap.add_argument("--prefetch-spinors", type=int, default=0,
+                    help="--case mhat: next hop's spinor prefetched in registers (tuner off)")
     return ap.parse_args()
 
 
@@ -484,6 +487,7 @@ def run_mhat_case(args):
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_PAIRED_RHS, args.paired_rhs)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_BLOCKED_TILES, args.blocked_tiles)
     ctx.wcl_set_option(pkg.wcl.WCL_OPT_TMA_STAGING, args.tma_staging)
+    ctx.wcl_set_option(pkg.wcl.WCL_OPT_PREFETCH_SPINORS, args.prefetch_spinors)
     ctx.wcl_load_gauge(torch.from_numpy(W.gauge_links(dims, EPS, SEED)).cuda(), KAPPA, CSW)
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     psi = torch.from_numpy(W.gaussian_fermion(dims, 1, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(-1)
@@ -502,7 +506,7 @@ def run_mhat_case(args):
                       "tensor_cores": args.tensor_cores, "shared_links": args.shared_links,
                       "staged_spinors": args.staged_spinors, "autotune": args.autotune,
                       "paired_rhs": args.paired_rhs, "blocked_tiles": args.blocked_tiles,
-                      "tma_staging": args.tma_staging,
+                      "tma_staging": args.tma_staging, "prefetch_spinors": args.prefetch_spinors,
                       "dslash_launches": st["dslash_timed"], "avg_launch_ms": st["dslash_ms"] / st["dslash_timed"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind}))
     ctx.close()

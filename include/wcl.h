@@ -341,8 +341,9 @@ typedef enum {
   WCL_OPT_TMA_STAGING = 9 /* 1: when the tuner is off, the multi-RHS FP32 dslash on a lattice with Lx = 32
                              runs the persistent kernel whose tiles are whole x-rows and whose links and
                              clover reach shared memory by tensor copies (TMA, cp.async.bulk.tensor),
-                             double buffered under the previous tile's compute; 0 (default): ordinary
-                             loads.  With the tuner on, both are candidates where the kernel applies. */
+                             double buffered under the previous tile's compute; 2: the same kernel with
+                             one CTA per tile (copies issued at its start); 0 (default): ordinary loads.
+                             With the tuner on, all are candidates where the kernel applies. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

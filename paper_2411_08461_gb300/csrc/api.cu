@@ -524,7 +524,12 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
     case WCL_OPT_BLOCKED_TILES: c->blocked_tiles = value != 0; return WCL_OK;
     case WCL_OPT_PAIRED_RHS: c->paired_rhs = value != 0; return WCL_OK;
     case WCL_OPT_PREFETCH_SPINORS: c->prefetch_spinors = value != 0; return WCL_OK;
-    case WCL_OPT_TMA_STAGING: c->tma_staging = value != 0; return WCL_OK;
+    case WCL_OPT_TMA_STAGING:
+      if (value >= 0 && value <= 2) {
+        c->tma_staging = value;
+        return WCL_OK;
+      }
+      break;
   }
   set_error("wcl_set_option: unknown option %d or value %d", option, value);
   return WCL_ERR_INVALID_ARG;

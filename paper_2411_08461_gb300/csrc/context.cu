@@ -175,8 +175,9 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   }
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
-  if (ch.variant == V_TMA) return prec == F32 ? launch_dslash_tma(a, dagger, mode, st, ctxs[0]->d_flags)
-                                               : cudaErrorInvalidValue;
+  if (ch.variant == V_TMA || ch.variant == V_TMA_TILE)
+    return prec == F32 ? launch_dslash_tma(a, dagger, mode, st, ctxs[0]->d_flags, ch.variant == V_TMA)
+                       : cudaErrorInvalidValue;
   if (ch.variant == V_PAIR || ch.variant == V_PAIR_ZB) {
     switch (prec) {
       case F32: return launch_dslash_pair<F32>(a, dagger, mode, ts, st);
@@ -221,7 +222,7 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
   if (tc_ok)
     dflt = {V_TC, tc_tile_sites()};
   else if (tma_ok && c0->tma_staging)
-    dflt = {V_TMA, 16};
+    dflt = {c0->tma_staging == 2 ? V_TMA_TILE : V_TMA, 16};
   else if (pair_ok && c0->paired_rhs)
     dflt = c0->blocked_tiles ? TuneChoice{V_PAIR_ZB, 16} : TuneChoice{V_PAIR, c0->shared_links};
   else if (mr_ok && c0->staged_spinors && prec != F64)
@@ -269,7 +270,10 @@ static TuneChoice choose_variant(const std::vector<wcl_ctx*>& ctxs, int prec, in
     }
     if (zb) cand.push_back({V_SMEM_ZB, 16});
     if (zb && prec != F64) cand.push_back({V_SMEM_PF_ZB, 16});
-    if (tma_ok) cand.push_back({V_TMA, 16});
+    if (tma_ok) {
+      cand.push_back({V_TMA, 16});
+      cand.push_back({V_TMA_TILE, 16});
+    }
     if (pair_ok) {
       for (int ts : {8, 16, 32}) cand.push_back({V_PAIR, ts});
       if (zb) cand.push_back({V_PAIR_ZB, 16});

@@ -64,7 +64,8 @@ struct wcl_ctx {
   bool blocked_tiles = false;    // untuned multi-RHS dslash: tiles in z blocks (large lattices)
   bool paired_rhs = false;       // untuned multi-RHS FP32/16-bit dslash: the packed-pair kernel
   bool prefetch_spinors = false; // untuned multi-RHS dslash: next hop's spinor prefetched in registers
-  bool tma_staging = false;      // untuned multi-RHS FP32 dslash: links and clover staged by TMA
+  int tma_staging = 0;           // untuned multi-RHS FP32 dslash: links and clover staged by TMA
+                                 // (1 persistent CTAs, 2 one CTA per tile)
   int blas_block = 256;
   void* mg = nullptr;    // multigrid hierarchy (mg.cu), built by wcl_mg_setup
   void* stag = nullptr;  // staggered links and mass (stag.cu), loaded by wcl_load_staggered
@@ -168,11 +169,11 @@ bool use_tc(const wcl_ctx* c, int prec, int nrhs, int mode);
 // loaded into registers while the current hop is computed
 enum TuneVariant {
   V_THREAD = 0, V_SMEM = 1, V_TC = 2, V_SMEM_ASYNC = 3, V_SMEM_ZB = 4, V_PAIR = 5, V_PAIR_ZB = 6, V_SMEM_PF = 7,
-  V_SMEM_PF_ZB = 8, V_TMA = 9
+  V_SMEM_PF_ZB = 8, V_TMA = 9, V_TMA_TILE = 10
 };
 // TMA-staged persistent multi-RHS kernel (dslash_tma.cu): FP32, one lattice with Lx = 32
 bool tma_eligible(const LatGeom& g, int nrhs);
-cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaStream_t st, int* err);
+cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaStream_t st, int* err, bool persistent);
 struct TuneChoice {
   int variant;  // TuneVariant
   int block;    // threads per CTA (V_THREAD) or sites per CTA (V_SMEM, V_SMEM_ASYNC, V_TC)

@@ -300,8 +300,10 @@ bool tma_eligible(const LatGeom& g, int nrhs) {
     fin = EPI;                                                                                   \
     break;
 
-// a.b must describe one lattice with tiles of 16 sites (one x-row each)
-cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaStream_t st, int* err) {
+// a.b must describe one lattice with tiles of 16 sites (one x-row each); persistent: five
+// CTAs per SM walking the rows with the next row's copies in flight, else one CTA per row
+// (its copies issued at its start, no overlap within the CTA)
+cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaStream_t st, int* err, bool persistent) {
   const LatGeom& g = a.b.lat[0];
   if (a.b.nlat != 1 || !tma_eligible(g, a.nrhs_tc)) return cudaErrorInvalidValue;
   const int p = a.out_parity;
@@ -315,7 +317,7 @@ cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaSt
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long nrows = g.vh / TMA_TS;
-  const int grid = (int)std::min<long>(nrows, (long)nsm * 5);
+  const int grid = persistent ? (int)std::min<long>(nrows, (long)nsm * 5) : (int)nrows;
   int fin = 0;
   switch (mode | (dagger ? 16 : 0)) {
     WCL_TMA_CASE(false, MODE_POST, EPI_NONE)

@@ -40,7 +40,7 @@ void load_file() {
     if (std::sscanf(line, "%d %d %f %n", &v, &b, &ms, &n) != 3 || n <= 0) continue;
     std::string key = line + n;
     while (!key.empty() && (key.back() == '\n' || key.back() == '\r')) key.pop_back();
-    if (v < V_THREAD || v > V_TMA || b <= 0 || b > 1024 || key.empty()) continue;
+    if (v < V_THREAD || v > V_TMA_TILE || b <= 0 || b > 1024 || key.empty()) continue;
     g_cache[key] = TuneChoice{v, b};
   }
   std::fclose(f);

@@ -199,9 +199,10 @@ def test_multi_rhs_paired_blocked_tile_order(pkg, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("dagger", [False, True])
 @pytest.mark.parametrize("dims,nrhs", [((32, 4, 2, 4), 12), ((32, 2, 2, 6), 4), ((32, 4, 4, 2), 7), ((32, 6, 2, 2), 16)])
-def test_apply_Mpc_multi_rhs_tma_staged(pkg, dims, nrhs, dagger):
+def test_apply_Mpc_multi_rhs_tma_staged(pkg, dims, nrhs, dagger, mode):
     """The persistent FP32 kernel whose links and clover arrive by tensor copies (TMA),
     tiles = whole x-rows of 16 sites (Lx = 32), two stages in flight; more rows than
     CTAs only on the larger shapes, so both one and several tiles per CTA are covered."""
@@ -209,7 +210,7 @@ def test_apply_Mpc_multi_rhs_tma_staged(pkg, dims, nrhs, dagger):
 
     ctx, op, _ = _setup(pkg, dims, seed=33)
     ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
-    ctx.wcl_set_option(WCL_OPT_TMA_STAGING, 1)
+    ctx.wcl_set_option(WCL_OPT_TMA_STAGING, mode)
     psi = W.gaussian_fermion(dims, 34, nrhs=nrhs)[:, 0].copy()
     psi[1] *= 1e-7
     out = cuda(np.zeros_like(psi))
@@ -230,12 +231,12 @@ def test_tma_staged_many_tiles_per_cta(pkg):
     ctx.wcl_set_option(WCL_OPT_AUTOTUNE, 0)
     psi = cuda(W.gaussian_fermion(dims, 36, nrhs=12)[:, 0].copy())
     outs = []
-    for tma in (1, 0):
+    for tma in (1, 2, 0):
         ctx.wcl_set_option(WCL_OPT_TMA_STAGING, tma)
         o = cuda(np.zeros(psi.shape, dtype=np.complex128))
         ctx.wcl_apply_Mpc(o, psi, "f32", nrhs=12)
         outs.append(host(o))
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[2])
     ctx.close()
 
 
@@ -277,7 +278,8 @@ def test_autotuner_choice_and_cache_file(pkg, tmp_path, monkeypatch):
     assert len(lines) == 2, lines  # the two launches of M_hat, each tuned once
     for v, b, ms, *_ in lines:
         assert (int(v), int(b)) in {(0, 64), (0, 128), (0, 256), (0, 512), (1, 8), (1, 16), (1, 32), (3, 16),
-                                    (4, 16), (5, 8), (5, 16), (5, 32), (6, 16), (7, 16), (8, 16), (9, 16)}
+                                    (4, 16), (5, 8), (5, 16), (5, 32), (6, 16), (7, 16), (8, 16), (9, 16),
+                                    (10, 16)}
         assert float(ms) > 0
 
 
