@@ -121,17 +121,12 @@ __global__ void __launch_bounds__(256, 4)
     fence_proxy_async();  // the barriers' initialisation is visible to the copy engine
   }
   __syncthreads();
-  // each CTA walks one contiguous run of rows, so that the rows in flight on the GPU at
-  // any time are the neighbours (in y, z and t) of rows recently read by other CTAs
-  const long per = (nrows + gridDim.x - 1) / gridDim.x;
-  const long first = (long)blockIdx.x * per;
-  const long last = first + per < nrows ? first + per : nrows;
-  long row = first;
-  if (threadIdx.x == 0 && row < last) tma_issue(maps, g, row, raw[0], &bar[0]);
-  for (int it = 0; row < last; it++, row++) {
+  long row = blockIdx.x;
+  if (threadIdx.x == 0 && row < nrows) tma_issue(maps, g, row, raw[0], &bar[0]);
+  for (int it = 0; row < nrows; it++, row += gridDim.x) {
     const int st = it & 1;
-    const long next = row + 1;
-    if (threadIdx.x == 0 && next < last) {
+    const long next = row + gridDim.x;
+    if (threadIdx.x == 0 && next < nrows) {
       fence_proxy_async();  // the stage being refilled was last read by ordinary loads
       tma_issue(maps, g, next, raw[st ^ 1], &bar[st ^ 1]);
     }
@@ -306,8 +301,8 @@ bool tma_eligible(const LatGeom& g, int nrhs) {
     break;
 
 // a.b must describe one lattice with tiles of 16 sites (one x-row each); persistent: five
-// CTAs per SM, each walking a contiguous run of rows with the next row's copies in flight,
-// else one CTA per row (its copies issued at its start, no overlap within the CTA)
+// CTAs per SM walking the rows with the next row's copies in flight, else one CTA per row
+// (its copies issued at its start, no overlap within the CTA)
 cudaError_t launch_dslash_tma(const DslashArgs& a, bool dagger, int mode, cudaStream_t st, int* err, bool persistent) {
   const LatGeom& g = a.b.lat[0];
   if (a.b.nlat != 1 || !tma_eligible(g, a.nrhs_tc)) return cudaErrorInvalidValue;
