@@ -650,8 +650,9 @@ def run_throughput_case(args):
 
 def run_precond_case(args):
     """Apply the learned preconditioner's PTC network (random weights of the trained
-    shape) to --nrhs Gaussian fields on --lattice: FP32 SIMT layers, BF16 SIMT layers
-    and BF16 tensor-core layers; CUDA-event time per application."""
+    shape) to --nrhs Gaussian fields on --lattice: FP32 SIMT layers, BF16 SIMT layers,
+    BF16 layers on mma.sync and on tcgen05 (inputs split into 3, 2 or 1 BF16 terms);
+    CUDA-event time per application."""
     import torch
 
     import workloads as W
@@ -667,8 +668,11 @@ def run_precond_case(args):
     r = torch.from_numpy(W.gaussian_fermion(dims, 2, nrhs=args.nrhs)[:, 0].copy()).cuda().reshape(args.nrhs, vh * 12)
     z = torch.empty_like(r)
     res = {"case": "precond", "lattice": dims, "nrhs": args.nrhs}
-    for name, bf16, tc in (("fp32_simt", 0, 0), ("bf16_simt", 1, 0), ("bf16_tensor_cores", 1, 1)):
+    for name, bf16, tc, split in (("fp32_simt", 0, 0, 3), ("bf16_simt", 1, 0, 3), ("bf16_tensor_cores", 1, 1, 3),
+                                  ("bf16_tcgen05", 1, 2, 3), ("bf16_tcgen05_split2", 1, 2, 2),
+                                  ("bf16_tcgen05_split1", 1, 2, 1)):
         ctx.wcl_set_option(pkg.wcl.WCL_OPT_PTC_TENSOR_CORES, tc)
+        ctx.wcl_set_option(pkg.wcl.WCL_OPT_PTC_SPLIT, split)
         for _ in range(max(1, args.warmup)):
             ctx.wcl_precond_apply(z, r, args.nrhs, bf16=bf16)
         torch.cuda.synchronize()

@@ -309,10 +309,14 @@ typedef enum {
                           for the process; the environment variable WCL_TUNE_CACHE=<file>
                           makes the choices persist (text, appended).  0: fixed defaults */
   ,
-  WCL_OPT_PTC_TENSOR_CORES = 4 /* 1 (default): the learned preconditioner's BF16 layers do the
-                                  channel and spin mixing on the tensor cores (mma.sync, BF16
-                                  weights, inputs split into three BF16 terms, FP32 accumulation);
-                                  0: FP32 SIMT mixing */
+  WCL_OPT_PTC_TENSOR_CORES = 4 /* how the learned preconditioner's BF16 layers do the channel
+                                  and spin mixing (BF16 weights, FP32 accumulation): 2 (default)
+                                  on the fifth-generation tensor cores (tcgen05: one CTA per 128
+                                  sites, operands in shared memory, accumulators in tensor memory;
+                                  inputs as WCL_OPT_PTC_SPLIT BF16 terms; a bounded wait that
+                                  expires makes the call return WCL_ERR_TIMEOUT); 1: mma.sync,
+                                  inputs split into three BF16 terms; 0: FP32 SIMT mixing.  Other
+                                  values: WCL_ERR_INVALID_ARG */
   ,
   WCL_OPT_STAGED_SPINORS = 5 /* 1: when the tuner is off, the multi-RHS dslash (16-site tiles)
                                 also stages each thread's neighbour spinors in shared memory with
@@ -344,6 +348,13 @@ typedef enum {
                              double buffered under the previous tile's compute; 2: the same kernel with
                              one CTA per tile (copies issued at its start); 0 (default): ordinary loads.
                              With the tuner on, all are candidates where the kernel applies. */
+  ,
+  WCL_OPT_PTC_SPLIT = 10 /* BF16 terms each transported input is split into on the tcgen05 network
+                            layers (WCL_OPT_PTC_TENSOR_CORES = 2): 1 (default, plain BF16 inputs),
+                            2 (16 significant bits) or 3 (24 bits: the FP32 layer to FP32 rounding);
+                            fewer terms need less shared memory per CTA and fewer MMAs.  The
+                            network is a preconditioner of flexible GCR, whose true residual does
+                            not depend on it. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

@@ -36,6 +36,25 @@ wcl_status wcl_leave(wcl_ctx* c, wcl_status s) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->user_stream, c->ev_out, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess && s == WCL_OK) return cuda_fail(e, "cudaStreamSynchronize");
+  if (e == cudaSuccess && c->wait_check) {
+    // bits 0x100 (TMA-staged dslash) and 0x200 (tcgen05 network layer): a CTA gave up
+    // on an mbarrier wait and left its outputs unwritten
+    c->wait_check = false;
+    e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return s == WCL_OK ? cuda_fail(e, "reading the device error word") : s;
+    const int f = c->h_flags[0];
+    if (f & 0x300) {
+      c->h_flags[0] = f & ~0x300;
+      e = cudaMemcpyAsync(c->d_flags, c->h_flags, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (s == WCL_OK) {
+        set_error("a bounded mbarrier wait expired in the %s; its outputs were not written",
+                  (f & 0x200) ? "tcgen05 network layer" : "TMA-staged dslash");
+        s = WCL_ERR_TIMEOUT;
+      }
+    }
+  }
   return s;
 }
 
@@ -519,7 +538,10 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
       }
       break;
     case WCL_OPT_AUTOTUNE: c->autotune = value != 0; return WCL_OK;
-    case WCL_OPT_PTC_TENSOR_CORES: c->ptc_tensor_cores = value != 0; return WCL_OK;
+    case WCL_OPT_PTC_TENSOR_CORES:
+      if (value < 0 || value > 2) break;
+      c->ptc_tensor_cores = value;
+      return WCL_OK;
     case WCL_OPT_STAGED_SPINORS: c->staged_spinors = value != 0; return WCL_OK;
     case WCL_OPT_BLOCKED_TILES: c->blocked_tiles = value != 0; return WCL_OK;
     case WCL_OPT_PAIRED_RHS: c->paired_rhs = value != 0; return WCL_OK;
@@ -527,6 +549,12 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
     case WCL_OPT_TMA_STAGING:
       if (value >= 0 && value <= 2) {
         c->tma_staging = value;
+        return WCL_OK;
+      }
+      break;
+    case WCL_OPT_PTC_SPLIT:
+      if (value >= 1 && value <= 3) {
+        c->ptc_split = value;
         return WCL_OK;
       }
       break;

@@ -175,9 +175,11 @@ static cudaError_t launch_variant(const std::vector<wcl_ctx*>& ctxs, int prec, i
   }
   a.nrhs_tc = nrhs;
   if (ch.variant == V_TC) return launch_dslash_tc(prec, a, dagger, mode, st);
-  if (ch.variant == V_TMA || ch.variant == V_TMA_TILE)
-    return prec == F32 ? launch_dslash_tma(a, dagger, mode, st, ctxs[0]->d_flags, ch.variant == V_TMA)
-                       : cudaErrorInvalidValue;
+  if (ch.variant == V_TMA || ch.variant == V_TMA_TILE) {
+    if (prec != F32) return cudaErrorInvalidValue;
+    ctxs[0]->wait_check = true;
+    return launch_dslash_tma(a, dagger, mode, st, ctxs[0]->d_flags, ch.variant == V_TMA);
+  }
   if (ch.variant == V_PAIR || ch.variant == V_PAIR_ZB) {
     switch (prec) {
       case F32: return launch_dslash_pair<F32>(a, dagger, mode, ts, st);

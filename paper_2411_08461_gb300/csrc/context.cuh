@@ -59,7 +59,9 @@ struct wcl_ctx {
   int shared_links = 16;      // multi-RHS dslash with links/clover staged in shared memory:
                               // 0 off, else its sites per CTA when the tuner does not choose
   bool autotune = true;       // time the dslash variants of a new configuration on first use
-  bool ptc_tensor_cores = true;  // BF16 network layers mix channels on the tensor cores
+  int ptc_tensor_cores = 2;  // BF16 network layers' mixing: 0 SIMT, 1 mma.sync, 2 tcgen05
+  int ptc_split = 1;         // BF16 terms per transported input on the tcgen05 layers
+  bool wait_check = false;    // a kernel with bounded mbarrier waits ran since the last API return
   bool staged_spinors = false;   // untuned multi-RHS dslash: cp.async-staged neighbour spinors
   bool blocked_tiles = false;    // untuned multi-RHS dslash: tiles in z blocks (large lattices)
   bool paired_rhs = false;       // untuned multi-RHS FP32/16-bit dslash: the packed-pair kernel

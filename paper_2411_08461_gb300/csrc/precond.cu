@@ -238,8 +238,27 @@ static wcl_status layer_both(const std::vector<wcl_ctx*>& ctxs, int nrhs, const 
   a.cin = cin;
   a.cout = cout;
   a.use_bf16 = use_bf16;
+  if (use_bf16 && c0->ptc_tensor_cores == 2) {
+    // tcgen05 layers: 128-site tiles, B operands of the nine shifts packed once per layer
+    a.b = make_batch(ctxs, nrhs, ptc_umma_sites_per_cta(), 0);
+    void* q;
+    WCL_CHECK(ws_get(c0, "ptc_umma_b", ptc_umma_pack_bytes(PTC_MAXC, PTC_MAXC), &q));
+    uint4* bp = static_cast<uint4*>(q);
+    cudaError_t e = ptc_pack_umma(wb, cin, cout, bp, c0->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ptc tcgen05 operand packing");
+    count_launch(c0);
+    c0->wait_check = true;
+    for (int p = 0; p < 2; p++) {
+      if (only_parity >= 0 && p != only_parity) continue;
+      a.parity = p;
+      e = ptc_layer_umma(a, bp, c0->ptc_split, c0->d_flags, c0->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "ptc tcgen05 layer launch");
+      count_launch(c0);
+    }
+    return WCL_OK;
+  }
   uint4* frag = nullptr;
-  if (use_bf16 && c0->ptc_tensor_cores) {
+  if (use_bf16 && c0->ptc_tensor_cores == 1) {
     void* q;
     WCL_CHECK(ws_get(c0, "ptc_frag", sizeof(uint4) * ptc_frag_entries(PTC_MAXC, PTC_MAXC), &q));
     frag = static_cast<uint4*>(q);

@@ -1,4 +1,5 @@
 // PTC network layer and weight-gradient kernels (see ptc.cuh).
+#include "blackwell.cuh"
 #include "ptc.cuh"
 
 namespace wcl {
@@ -349,6 +350,245 @@ cudaError_t ptc_layer(const PtcLayerArgs& a, cudaStream_t st, const uint4* frag)
     ptc_layer_kernel<<<a.b.total_blocks, 4 * PTC_SITES_PER_CTA, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fifth-generation tensor-core layer (tcgen05, BF16 weights).  One CTA per tile of 128
+// sites of one (lattice, rhs) slice and output parity; the sites are the M = 128 rows
+// of the MMA.  For every shift s and colour c the mixing is the real GEMM
+//   D_c[site][(co, alpha, re/im)] += sum_k X_{s,c}[site][k] B_s[(co, alpha, re/im)][k],
+//   k = (ci, beta, re/im),
+// with B_s the weights W[co][ci][s] in real form [[Re, -Im], [Im, Re]] (exact in BF16;
+// N = 8 cout and K = 8 cin, each padded to 16) and X_{s,c} the transported inputs of
+// colour c, split into NPART BF16 terms (hi + mid + lo carry 24 significant bits), each
+// its own K block of the same B.  The SIMT threads compute the transports (gathers and
+// link multiplies, as in the layers above) and write X in the no-swizzle K-major
+// core-matrix layout of blackwell.cuh, where the eight values (beta, re/im) of one
+// (site, ci, colour) are exactly one 16-byte core-matrix row.  One thread issues the
+// 3 x NPART x K/16 MMAs of a shift (descriptors into shared memory, accumulators in
+// tensor memory: colour c in columns [c N, (c + 1) N)) and commits them to an mbarrier;
+// the X buffer is rewritten for the next shift once that mbarrier's phase completes,
+// with the next shift's gathers already issued.  After the ninth shift every warp
+// reads its lane quarter of the accumulators (tcgen05.ld) and stores whole spinors of
+// one output channel.  Every mbarrier wait is bounded: on expiry the CTA stops issuing,
+// waits (bounded) for its MMAs in flight, frees its tensor memory, sets bit 0x200 of
+// the error word and leaves its outputs unwritten.
+constexpr int UPTC_SITES = 128;
+constexpr int UPTC_THREADS = 256;
+constexpr unsigned UPTC_TMEM_COLS = 128;  // 3 colours x N <= 96 columns
+constexpr long UPTC_WAIT_LIMIT = 1L << 22;
+
+__host__ __device__ inline int uptc_n(int cout) { return cout * 8 < 16 ? 16 : cout * 8; }
+__host__ __device__ inline int uptc_k(int cin) { return cin * 8 < 16 ? 16 : cin * 8; }
+
+// B operands of the nine shifts, [shift][N / 8][K / 8][8][8] BF16
+__global__ void ptc_pack_umma_kernel(const __nv_bfloat162* __restrict__ wb, int cin, int cout,
+                                     __nv_bfloat16* __restrict__ out) {
+  const int nn = uptc_n(cout), kk = uptc_k(cin), per = nn * kk;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= PTC_NSHIFT * per) return;
+  const int sh = e / per, r = e - sh * per;
+  const int n = r / kk, k = r - n * kk;
+  const int co = n >> 3, al = (n >> 1) & 3, ro = n & 1;
+  const int ci = k >> 3, be = (k >> 1) & 3, ri = k & 1;
+  float v = 0.f;
+  if (co < cout && ci < cin) {
+    const float2 w = __bfloat1622float2(wb[((co * cin + ci) * PTC_NSHIFT + sh) * 16 + al * 4 + be]);
+    v = ro == 0 ? (ri == 0 ? w.x : -w.y) : (ri == 0 ? w.y : w.x);
+  }
+  out[sh * per + ((n >> 3) * (kk >> 3) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+}
+
+// eight floats -> NPART rows of eight BF16 whose sum carries 8 NPART significant bits
+template <int NPART>
+__device__ __forceinline__ void split_row(const float v[8], uint4 out[NPART]) {
+  float rest[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) rest[k] = v[k];
+#pragma unroll
+  for (int part = 0; part < NPART; part++) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(rest[2 * k], rest[2 * k + 1]);
+      const float2 f = __bfloat1622float2(h);
+      rest[2 * k] -= f.x;
+      rest[2 * k + 1] -= f.y;
+      w[k] = bf16x2_bits(h);
+    }
+    out[part] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int NPART>
+__global__ void __launch_bounds__(UPTC_THREADS, NPART == 3 ? 2 : NPART == 2 ? 3 : 4)
+    ptc_layer_umma_kernel(const __grid_constant__ PtcLayerArgs a, const uint4* __restrict__ bpack, int* err) {
+  extern __shared__ __align__(128) unsigned char uptc_smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int nn = uptc_n(a.cout), kk = uptc_k(a.cin);
+  const int xbytes = UPTC_SITES * kk * 2;  // one (part, colour) X operand
+  const int bshift = nn * kk * 2;          // one shift's B operand
+  unsigned char* X = uptc_smem;
+  unsigned char* Bs = uptc_smem + NPART * 3 * xbytes;
+  // K columns of absent input channels stay zero; B is copied once for all shifts
+  for (int k = threadIdx.x; k < NPART * 3 * xbytes / 16; k += blockDim.x)
+    reinterpret_cast<uint4*>(X)[k] = make_uint4(0u, 0u, 0u, 0u);
+  for (int k = threadIdx.x; k < PTC_NSHIFT * bshift / 16; k += blockDim.x) reinterpret_cast<uint4*>(Bs)[k] = bpack[k];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (threadIdx.x < 32) tmem_alloc(&tslot, UPTC_TMEM_COLS);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tbase = tslot;
+
+  const Slice s = find_slice(a.b, blockIdx.x);
+  const LatGeom& g = a.b.lat[s.l];
+  const int row = threadIdx.x & (UPTC_SITES - 1), half = threadIdx.x >> 7;  // site row; channels half, half + 2
+  const long i = (long)s.chunk * UPTC_SITES + row;
+  const bool site_ok = i < g.vh;
+  const long ii = site_ok ? i : 0;
+  const long stride = g.stride;
+  const int p = a.parity;
+  const Nbr n = neighbours(g, p, ii);
+  const void* g_here = a.gauge[s.l][p];
+  const void* g_there = a.gauge[s.l][1 - p];
+  // byte offset of this site's row in K group 0 of an X operand
+  const int xrow = ((row >> 3) * (kk >> 3)) * 128 + (row & 7) * 16;
+  const uint32_t idesc = idesc_bf16_f32(UPTC_SITES, nn);
+  const unsigned x0 = smem_u32(X), b0 = smem_u32(Bs), sbo = (unsigned)(kk >> 3) * 128u;
+
+  auto put = [&](const cpx<float> t[12], int ci) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float v[8];
+#pragma unroll
+      for (int be = 0; be < 4; be++) {
+        v[2 * be] = t[3 * be + c].re;
+        v[2 * be + 1] = t[3 * be + c].im;
+      }
+      uint4 parts[NPART];
+      split_row<NPART>(v, parts);
+#pragma unroll
+      for (int part = 0; part < NPART; part++)
+        *reinterpret_cast<uint4*>(X + (part * 3 + c) * xbytes + xrow + ci * 128) = parts[part];
+    }
+  };
+  auto fetch = [&](cpx<float> t[12], int sh, int ci) {
+    if (site_ok) {
+      const float4* fh = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, p, stride);
+      const float4* ft = a.in[s.l] + ptc_field_offset(s.rhs, ci, a.cin, 1 - p, stride);
+      transport(t, sh, fh, ft, g_here, g_there, stride, ii, n);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) t[k] = {0.f, 0.f};
+    }
+  };
+
+  int issued = 0;  // shifts whose MMAs were committed
+  bool ok = true;
+#pragma unroll 1
+  for (int sh = 0; sh < PTC_NSHIFT; sh++) {
+    int timeout = 0;
+    cpx<float> t[12];
+    if (half < a.cin) fetch(t, sh, half);
+    // the X buffer is free once the previous shift's MMAs have completed
+    if (sh > 0 && !mbar_wait_bounded(&bar, (unsigned)(sh - 1) & 1u, UPTC_WAIT_LIMIT)) timeout = 1;
+    if (!timeout) {
+      if (half < a.cin) put(t, half);
+      if (half + 2 < a.cin) {
+        fetch(t, sh, half + 2);
+        put(t, half + 2);
+      }
+    }
+    fence_proxy_async();  // X written by ordinary stores, read by the tensor core
+    tc_fence_before_sync();
+    if (__syncthreads_or(timeout)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after_sync();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int part = 0; part < NPART; part++)
+          for (int j = 0; j < (kk >> 4); j++) {
+            const uint64_t ad = make_smem_desc(x0 + (unsigned)((part * 3 + c) * xbytes + j * 256), 128u, sbo);
+            const uint64_t bd = make_smem_desc(b0 + (unsigned)(sh * bshift + j * 256), 128u, sbo);
+            umma_bf16(tbase + (uint32_t)(c * nn), ad, bd, idesc, (sh | part | j) != 0);
+          }
+      umma_commit(&bar);
+    }
+    issued++;
+  }
+  // the last committed phase: every MMA of the CTA has completed
+  if (issued > 0 && !mbar_wait_bounded(&bar, (unsigned)(issued - 1) & 1u, UPTC_WAIT_LIMIT)) ok = false;
+  ok = __syncthreads_and(ok) != 0;
+  tc_fence_after_sync();
+  if (ok) {
+    const uint32_t lane_base = (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
+#pragma unroll 1
+    for (int co = half; co < a.cout; co += 2) {
+      float v[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; c++) tmem_ld8(tbase + lane_base + (uint32_t)(c * nn + co * 8), v[c]);
+      tmem_ld_wait();
+      cpx<float> o12[12];
+#pragma unroll
+      for (int al = 0; al < 4; al++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) o12[3 * al + c] = {v[c][2 * al], v[c][2 * al + 1]};
+      if (site_ok) {
+        float4* o = a.out[s.l] + ptc_field_offset(s.rhs, co, a.cout, p, stride);
+        if (a.accumulate) {
+          cpx<float> prev[12];
+          SpinorIO<F32>::load<false>(prev, o, nullptr, stride, i);
+#pragma unroll
+          for (int k = 0; k < 12; k++) o12[k] = o12[k] + prev[k];
+        }
+        SpinorIO<F32>::store(o12, o, nullptr, stride, i);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(err, 0x200);
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after_sync();
+    tmem_dealloc(tbase, UPTC_TMEM_COLS);
+  }
+}
+
+int ptc_umma_sites_per_cta() { return UPTC_SITES; }
+size_t ptc_umma_pack_bytes(int cin, int cout) { return (size_t)PTC_NSHIFT * uptc_n(cout) * uptc_k(cin) * 2; }
+
+cudaError_t ptc_pack_umma(const __nv_bfloat162* wb, int cin, int cout, uint4* out, cudaStream_t st) {
+  const int n = PTC_NSHIFT * uptc_n(cout) * uptc_k(cin);
+  ptc_pack_umma_kernel<<<(n + 255) / 256, 256, 0, st>>>(wb, cin, cout, reinterpret_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError();
+}
+
+template <int NPART>
+static cudaError_t launch_umma(const PtcLayerArgs& a, const uint4* bpack, int* err, cudaStream_t st) {
+  const size_t smem = (size_t)NPART * 3 * UPTC_SITES * uptc_k(a.cin) * 2 + ptc_umma_pack_bytes(a.cin, a.cout);
+  cudaError_t e = cudaFuncSetAttribute(ptc_layer_umma_kernel<NPART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  ptc_layer_umma_kernel<NPART><<<a.b.total_blocks, UPTC_THREADS, smem, st>>>(a, bpack, err);
+  return cudaGetLastError();
+}
+
+cudaError_t ptc_layer_umma(const PtcLayerArgs& a, const uint4* bpack, int nparts, int* err, cudaStream_t st) {
+  if (a.cout < 1 || a.cout > PTC_MAXC || a.cin < 1 || a.cin > PTC_MAXC || !bpack || !err) return cudaErrorInvalidValue;
+  if (nparts == 1) return launch_umma<1>(a, bpack, err, st);
+  if (nparts == 2) return launch_umma<2>(a, bpack, err, st);
+  if (nparts == 3) return launch_umma<3>(a, bpack, err, st);
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------

@@ -57,6 +57,14 @@ int ptc_layer_sites_per_cta();
 int ptc_frag_entries(int cin, int cout);
 cudaError_t ptc_pack_frag(const __nv_bfloat162* wb, int cin, int cout, uint4* frag, cudaStream_t st);
 
+// tcgen05 layer: a.b built with ptc_umma_sites_per_cta() sites per block; bpack the
+// layer's B operands (ptc_pack_umma, ptc_umma_pack_bytes bytes); nparts = 1, 2 or 3 BF16
+// terms per transported input; a wait that expires sets bit 0x200 of *err
+int ptc_umma_sites_per_cta();
+size_t ptc_umma_pack_bytes(int cin, int cout);
+cudaError_t ptc_pack_umma(const __nv_bfloat162* wb, int cin, int cout, uint4* out, cudaStream_t st);
+cudaError_t ptc_layer_umma(const PtcLayerArgs& a, const uint4* bpack, int nparts, int* err, cudaStream_t st);
+
 // dW[co][ci][s] += sum_x G_co(x) (T_s in_ci)(x)^+  (colour summed), per slice;
 // writes per-block partials [slot][ci*9+s][chunk][co][16] as float2 (FP32)
 struct PtcGradArgs {

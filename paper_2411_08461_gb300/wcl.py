@@ -32,6 +32,7 @@ WCL_OPT_BLOCKED_TILES = 6
 WCL_OPT_PAIRED_RHS = 7
 WCL_OPT_PREFETCH_SPINORS = 8
 WCL_OPT_TMA_STAGING = 9
+WCL_OPT_PTC_SPLIT = 10
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 
