@@ -22,6 +22,9 @@ The oracle is a plain, slow, direct transcription of the definitions:
                  M_hat^+ M_hat), to tell a well-posed workload from a near-singular draw.
 * ``staggered``- the staggered operator of the HISQ action on given fat and long links
                  (MILC phases), and its CG solve (Sec. II.A, II.E).
+* ``hisq``    -- the HISQ link smearing that makes those fat and long links from the thin
+                 links: fat7, U(3) projection, the second level with the Lepage and Naik
+                 terms (Sec. II.A).
 * ``multigrid``- aggregation multigrid preconditioner (null space, block prolongator,
                  Galerkin coarse operator, K-cycle) for flexible GCR (Sec. II.E, III.B).
 * ``residual`` -- the true residual ||b - M x|| / ||b|| of Eq. 5's operator evaluated one
@@ -33,4 +36,4 @@ lexicographic order (Lt, Lz, Ly, Lx, ...), converting to and from the QDP
 layout at the edges.  Which pins check each function is stated in its
 docstring; functions without a pin say "parity unpinned".
 """
-from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered, residual  # noqa: F401
+from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered, hisq, residual  # noqa: F401

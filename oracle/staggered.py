@@ -4,7 +4,7 @@ MILC staggered phase convention; Sec. II.E: CG is the default solver for HISQ).
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The operator takes the two
 link fields the HISQ smearing produces -- the fat links V (one-hop) and the long links
 W (three-hop, Naik coefficient included) -- as inputs; the smearing itself (fat7,
-U(3) projection, second level) is not part of this module.
+U(3) projection, second level) is oracle/hisq.py.
 
     M chi = 2 m chi + D chi
     D chi(x) = sum_mu eta_mu(x) [ V_mu(x) chi(x + mu) - V_mu(x - mu)^+ chi(x - mu)

@@ -6,10 +6,11 @@ import pytest
 
 import test_oracle_contract as TC
 import test_oracle_dirac as TD
+import test_oracle_hisq as THQ
 import test_oracle_multigrid as TM
 import test_oracle_ptc as TP
 import test_oracle_solvers as TS
-from oracle import contract, dirac, multigrid, ptc, solvers
+from oracle import contract, dirac, hisq, multigrid, ptc, solvers
 from oracle import lattice as L
 
 
@@ -208,3 +209,74 @@ def test_adam_second_moment_of_the_wrong_step(monkeypatch):
     monkeypatch.setattr(ptc, "adam_step", lambda w, g, s, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8:
                         orig(w, g, s, lr=lr, b1=b1, b2=b1, eps=eps))
     _fails(TP.test_adam_two_steps_closed_form)
+
+
+def test_hisq_seven_staple_coefficient(monkeypatch):
+    """1/192 instead of 1/384 for the 7-link staples of the first level."""
+    monkeypatch.setattr(hisq, "FAT7", (1 / 8, 1 / 16, 1 / 64, 1 / 192, 0.0))
+    _fails(THQ.test_abelian_flux_closed_form, 1)
+
+
+def test_hisq_lepage_sign(monkeypatch):
+    monkeypatch.setattr(hisq, "ASQ", (5 / 8, 1 / 16, 1 / 64, 1 / 384, 1 / 16))
+    _fails(THQ.test_abelian_flux_closed_form, 1)
+
+
+def test_hisq_backward_staple_end_point(monkeypatch):
+    """The backward staple closing at U_rho(x - rho) instead of U_rho(x - rho + mu)."""
+    orig = hisq.staple
+
+    def bad(U, mu, rho, sign, F):
+        if sign > 0:
+            return orig(U, mu, rho, sign, F)
+        back = hisq._shift(U[rho], rho, -1)
+        return hisq._dag(back) @ hisq._shift(F, rho, -1) @ back
+
+    monkeypatch.setattr(hisq, "staple", bad)
+    _fails(THQ.test_smearing_gauge_covariance, hisq.FAT7)
+
+
+def test_hisq_five_staples_one_ordering(monkeypatch):
+    """5-link staples summed over one ordering of each pair of directions only."""
+    def half_smear(U, coeffs):
+        c1, c3, c5, c7, cl = coeffs
+        out = np.empty_like(U)
+        for mu in range(4):
+            perp = [r for r in range(4) if r != mu]
+            acc = c1 * U[mu]
+            for rho in perp:
+                for s in (1, -1):
+                    acc = acc + c3 * hisq.staple(U, mu, rho, s, U[mu])
+                    for sig in perp:
+                        if sig <= rho:
+                            continue
+                        for s2 in (1, -1):
+                            acc = acc + c5 * hisq.staple(U, mu, rho, s, hisq.staple(U, mu, sig, s2, U[mu]))
+            out[mu] = acc
+        return out
+
+    monkeypatch.setattr(hisq, "smear", half_smear)
+    _fails(THQ.test_free_field, 0.0)
+
+
+def test_hisq_projection_power(monkeypatch):
+    """V (V^+ V)^(+1/2) instead of V (V^+ V)^(-1/2)."""
+    def bad(V):
+        lam, E = np.linalg.eigh(hisq._dag(V) @ V)
+        return V @ ((E * np.sqrt(lam)[..., None, :]) @ hisq._dag(E))
+
+    monkeypatch.setattr(hisq, "u3_project", bad)
+    _fails(THQ.test_u3_projection_is_the_polar_factor)
+
+
+def test_hisq_naik_shifted(monkeypatch):
+    """Naik link starting one site late: W(x + mu) W(x + 2 mu) W(x + 3 mu)."""
+    def bad(Wl):
+        out = np.empty_like(Wl)
+        for mu in range(4):
+            out[mu] = hisq._shift(Wl[mu], mu, 1) @ hisq._shift(Wl[mu], mu, 2) @ hisq._shift(Wl[mu], mu, 3)
+        return out
+
+    monkeypatch.setattr(hisq, "naik", bad)
+    _fails(THQ.test_naik_link_paths)
+    _fails(THQ.test_hisq_links_gauge_covariance)
