@@ -883,11 +883,13 @@ def run_compare_case(args):
 
 
 def run_staggered_case(args):
-    """Staggered operator M = 2 m + D of the HISQ action on given fat and long links
-    (synthetic: Gaussian complex matrices scaled by 0.3 and 0.05, mass 0.1) on --dims:
-    whole-lattice applies in FP64 and FP32 timed with CUDA events, algorithmic bytes per
-    output site = 16 links (each read once per launch) + the input vector + the output
-    (+ the 2 m x term), and one mixed-precision CG solve from a point source to --tol."""
+    """HISQ staggered workload on --dims (mass 0.1): the thin links of the seeded gauge
+    field (eps 0.3) smeared on the GPU into fat and long links (wcl_hisq_smear, FP64,
+    CUDA events; FP64 flops per site counted from its staple passes), the staggered
+    operator M = 2 m + D on those links, whole-lattice applies in FP64 and FP32
+    (algorithmic bytes per output site = 16 links read once per launch + the input
+    vector + the output + the 2 m x term), and one mixed-precision CG solve from a point
+    source to --tol."""
     import numpy as np
     import torch
 
@@ -904,15 +906,32 @@ def run_staggered_case(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = pkg.Context(dims, stream=stream)
-    rng_shape = (4, 2, lt, lz, ly, lx // 2, 3, 3)  # QDP gauge layout directly (synthetic values)
-    fat = torch.from_numpy(0.3 * W.gaussian_complex(rng_shape, 600)).to(dev)
-    lng = torch.from_numpy(0.05 * W.gaussian_complex(rng_shape, 601)).to(dev)
+    thin = torch.from_numpy(W.gauge_links(dims, EPS, SEED)).to(dev)
+    fat, lng = torch.empty_like(thin), torch.empty_like(thin)
+    ctx.wcl_hisq_smear(fat, lng, thin, 0.0)  # warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ctx.wcl_hisq_smear(fat, lng, thin, 0.0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    smear_ms = a.elapsed_time(b)
+    # FP64 flops per site: a one-sign staple is two 3x3 complex products (2 x 216); per
+    # link direction the first level runs 15 two-sign staple passes, the second 15 plus
+    # 12 one-sign Lepage passes; the U(3) projection about 750 per link, the Naik link 432
+    mm = 216
+    flops_site = 4 * (15 * 2 * 2 * mm) + 4 * (15 * 2 * 2 * mm + 12 * 2 * mm) + 4 * 750 + 4 * 2 * mm
     ctx.wcl_load_staggered(fat, lng, 0.1)
-    del fat, lng
+    del fat, lng, thin
     chi = torch.from_numpy(W.gaussian_complex((2, lt, lz, ly, lx // 2, 3), 602)).to(dev)
     out = torch.empty_like(chi)
     peak, kind = measured_peaks()
-    res = {"case": "staggered", "lattice": dims, "mass": 0.1, "peak": peak, "peak_kind": kind}
+    res = {"case": "staggered", "lattice": dims, "mass": 0.1, "peak": peak, "peak_kind": kind,
+           "links": "HISQ smearing of the eps 0.3 thin links on the GPU",
+           "hisq_smear": {"ms": smear_ms, "fp64_gflop": vol * flops_site / 1e9,
+                          "fp64_tflops": vol * flops_site / (smear_ms * 1e-3) / 1e12,
+                          "fp64_nominal_tflops": 1.25,
+                          "frac_of_nominal": vol * flops_site / (smear_ms * 1e-3) / 1e12 / 1.25}}
     for prec, real in (("f64", 8), ("f32", 4)):
         for _ in range(3):
             ctx.wcl_apply_staggered(out, chi, prec)

@@ -481,8 +481,28 @@ wcl_status wcl_mg_get_stencil(wcl_ctx* ctx, double* h_Y);
  * with V the fat (one-hop) and W the long (three-hop, Naik coefficient included) links of
  * the HISQ smearing, the MILC phases eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y),
  * eta_t = (-1)^(x+y+z), and t_boundary (wcl_create) on every hop across t = Lt-1 -> 0.
- * The smearing that produces V and W is the caller's.  Staggered fields are
+ * wcl_hisq_smear makes V and W from thin links.  Staggered fields are
  * [2][Lt][Lz][Ly][Lx/2][3] complex128 (QDP order, colour only), nrhs back to back. */
+
+/* HISQ link smearing in FP64 (Sec. II.A: the HISQ process of Follana et al. in the MILC
+ * convention, with a U(3) projection of the first fattened links; the paper gives no
+ * coefficients, these are the fat7 / asqtad ones).  With staple(+-rho, F) the mu-directed
+ * object F carried one step along +-rho and back, a smearing (c1, c3, c5, c7, cL) replaces
+ * each link by c1 U_mu + c3 sum of 3-link staples + c5 sum of 5-link staples (all ordered
+ * pairs of signed directions) + c7 sum of 7-link staples (ordered triples) + cL sum of the
+ * straight 5-link (Lepage) staples:
+ *   V = smear(U; 1/8, 1/16, 1/64, 1/384, 0),   W = V (V^+ V)^(-1/2),
+ *   fat = smear(W; 5/8, 1/16, 1/64, 1/384, -1/16) + eps/8 W,
+ *   long_mu(x) = -(1 + eps)/24 W_mu(x) W_mu(x+mu) W_mu(x+2mu),
+ * ready for wcl_load_staggered.  d_gauge: thin links U, QDP gauge layout [4][2][Lt][Lz][Ly]
+ * [Lx/2][3][3] complex128 (device or page-locked host, read only, periodic: no boundary
+ * sign); d_fat, d_long: caller-owned outputs in the same layout, written entirely (not
+ * valid after an error).  eps_naik: the Naik epsilon (0 for light quarks).  Uses ctx's
+ * lattice shape, device and stream, not its gauge field; allocates and frees about
+ * 15 x 144 bytes per site of work space during the call.  Errors: WCL_ERR_INVALID_ARG,
+ * WCL_ERR_NONFINITE (a non-finite thin link), WCL_ERR_RECONSTRUCT (a first-level link V
+ * with V^+ V not positive definite), WCL_ERR_OOM, WCL_ERR_CUDA. */
+wcl_status wcl_hisq_smear(wcl_ctx* ctx, void* d_fat, void* d_long, const void* d_gauge, double eps_naik);
 
 /* Load V and W (QDP gauge layout, complex128, device or page-locked host; any complex
  * 3x3 matrices) and the mass m (> 0: the solve is even-odd).  Kept in FP64 and FP32. */

@@ -120,6 +120,7 @@ SIGNATURES = {
     "wcl_contract": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
     "wcl_load_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "wcl_hisq_smear": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double]),
     "wcl_apply_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "wcl_invert_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_solve_params),
                                             ctypes.POINTER(wcl_solve_info)]),
@@ -296,6 +297,15 @@ class Context:
                "wcl_apply_Mpc_noalloc")
 
     # ---- staggered operator --------------------------------------------------------
+    def wcl_hisq_smear(self, fat, long_links, gauge, eps_naik: float = 0.0):
+        import torch
+
+        n = self.volume * 36
+        _check(load_library().wcl_hisq_smear(self.handle, _ptr(fat, torch.complex128, n, "fat", True),
+                                             _ptr(long_links, torch.complex128, n, "long", True),
+                                             _ptr(gauge, torch.complex128, n, "gauge", True), float(eps_naik)),
+               "wcl_hisq_smear")
+
     def wcl_load_staggered(self, fat, long_links, mass: float):
         import torch
 
