@@ -17,6 +17,8 @@
 //   mu=z: h0 = p0 + s i p2, h1 = p1 - s i p3;  rows 2,3 = -s i h0,  s i h1
 //   mu=t: h0 = p0 + s p2,   h1 = p1 + s p3;    rows 2,3 =  s h0,   s h1
 #pragma once
+#include <algorithm>
+
 #include "blas.cuh"
 #include "internal.cuh"
 
@@ -691,9 +693,14 @@ __device__ __forceinline__ void hop_from(cpx<R> acc[12], const cpx<R> psi[12], c
   reconstruct_acc<MU, S>(acc, uh);
 }
 
-// Register cap: 8- and 16-site tiles keep 64 registers per thread (five 192-thread
-// or ten 96-thread CTAs per SM for 12 RHS); 32-site tiles (up to 512 threads) are
-// capped at 128.
+// Register cap: every tile size keeps 64 registers per thread (five 192-thread or ten
+// 96-thread CTAs per SM for 12 RHS).  A 32-site CTA covers MR32_RPC right-hand sides
+// (the RHS of a tile are split over gridDim.y CTAs), so that each warp is 32 sites of
+// one RHS: a 16-byte shared-memory read of the staged links then returns 32 distinct
+// values in its four wavefronts, where a warp of 16 sites x 2 RHS reads every value
+// twice.  Each of the tile's CTAs stages the tile's links and clover (L2 hits after
+// the first).
+constexpr int MR32_RPC = 6;
 template <int TS>
 struct MrhsBounds;
 template <>
@@ -706,7 +713,7 @@ struct MrhsBounds<16> {
 };
 template <>
 struct MrhsBounds<32> {
-  static constexpr int THREADS = 512, MIN_BLOCKS = 1;
+  static constexpr int THREADS = 32 * MR32_RPC, MIN_BLOCKS = 5;
 };
 
 // ASYNC: the eight neighbour spinors of a thread are staged through shared memory
@@ -766,7 +773,14 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
     }
   }
   __syncthreads();
-  // phase 1: links and clover of the tile, unpacked to R
+  // phase 1: links and clover of the tile, unpacked to R.  Factors that are the
+  // same for every RHS are applied here, once per site instead of once per (site,
+  // RHS): the t-hop weights (boundary sign, anisotropy) go into the t links, and
+  // alpha goes into the links (XPAY) or into the clover term applied after the hops
+  // (POST); beta goes into the clover term applied to x (XPAY with PRE).
+  const R alpha = R(a.alpha[s.l]);
+  const R beta = R(a.beta[s.l]);
+  constexpr bool ALPHA_IN_LINKS = !(MODE & MODE_POST);
   for (int e = threadIdx.x; e < 8 * TS; e += blockDim.x) {
     const int ls = e % TS, d = e / TS, mu = d >> 1;
     const long i = site0 + ls;
@@ -781,16 +795,19 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
 #pragma unroll
       for (int k = 0; k < 9; k++) u[k / 3][k % 3] = {R(0), R(0)};
     }
+    R f = ALPHA_IN_LINKS ? alpha : R(1);
+    if (d >= 6) f = f * hop_t_weight<R>(g, (Tb[ls] & (d == 6 ? 1 : 2)) != 0);
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      Us[d][ls][2 * k] = u[k / 3][k % 3].re;
-      Us[d][ls][2 * k + 1] = u[k / 3][k % 3].im;
+      Us[d][ls][2 * k] = f * u[k / 3][k % 3].re;
+      Us[d][ls][2 * k + 1] = f * u[k / 3][k % 3].im;
     }
   }
   if (CLOV) {
     using CC = CloverChunk<P>;
     const void* cb = (MODE & MODE_POST) ? a.cpost[s.l] : a.cpre[s.l];
     const float* cn = (MODE & MODE_POST) ? a.cpost_norm[s.l] : a.cpre_norm[s.l];
+    const R cf = (MODE & MODE_POST) ? alpha : beta;
     for (int e = threadIdx.x; e < CC::NCH * TS; e += blockDim.x) {
       const int ls = e % TS, k = e / TS;
       const long i = site0 + ls;
@@ -802,13 +819,14 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
         for (int j = 0; j < CC::PER; j++) r[j] = R(0);
       }
 #pragma unroll
-      for (int j = 0; j < CC::PER; j++) Cs[CLOV ? ls : 0][CLOV ? CC::PER * k + j : 0] = r[j];
+      for (int j = 0; j < CC::PER; j++) Cs[CLOV ? ls : 0][CLOV ? CC::PER * k + j : 0] = cf * r[j];
     }
   }
   __syncthreads();
 
   // phase 2: thread = (site ls, rhs); the TS threads of one rhs are consecutive lanes
-  const int ls = threadIdx.x % TS, rhs = threadIdx.x / TS;
+  // (blockIdx.y > 0 only for 32-site tiles, whose RHS are split over CTAs)
+  const int ls = threadIdx.x % TS, rhs = (int)blockIdx.y * (int)(blockDim.x / TS) + (int)(threadIdx.x / TS);
   const long i = site0 + ls;
   double red[3] = {0.0, 0.0, 0.0};
   const bool valid = rhs < nrhs && i < g.vh && (!a.active || a.active[slot0 + rhs]);
@@ -818,9 +836,8 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
-    const int tb = Tb[ls];
-    const R sf = hop_t_weight<R>(g, tb & 1);
-    const R sb = hop_t_weight<R>(g, tb & 2);
+    // the t-hop weights are in the staged t links
+    const R sf = R(1), sb = R(1);
     if constexpr (ASYNC) {
       extern __shared__ uint4 stage_mem[];
       const int nt = blockDim.x;
@@ -887,16 +904,14 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
       hop_dir_smem<P, 2, DAG>(acc, in, in_norm, stride, Nb[4][ls], Nb[5][ls], Us[4][ls], Us[5][ls], R(1), R(1));
       hop_dir_smem<P, 3, DAG>(acc, in, in_norm, stride, Nb[6][ls], Nb[7][ls], Us[6][ls], Us[7][ls], sf, sb);
     }
-    const R alpha = R(a.alpha[s.l]);
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
+    // alpha is in the staged links, or (POST) in the staged clover term
     if (MODE & MODE_XPAY) {
       cpx<R> xv[12];
       SpinorIO<P>::load_cs(xv, rhs_ptr<P>(a.x, s.l, rhs, stride), rhs_norm(a.x, s.l, rhs, stride), stride, i);
-      const R beta = R(a.beta[s.l]);
       if (MODE & MODE_PRE) {
-        hermitian6_axpy_row(acc, beta, Cs[CLOV ? ls : 0], xv);
-        hermitian6_axpy_row(acc + 6, beta, Cs[CLOV ? ls : 0] + 36, xv + 6);
+        // beta is in the staged clover term
+        hermitian6_axpy_row(acc, R(1), Cs[CLOV ? ls : 0], xv);
+        hermitian6_axpy_row(acc + 6, R(1), Cs[CLOV ? ls : 0] + 36, xv + 6);
       } else {
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = acc[k] + beta * xv[k];
@@ -943,57 +958,75 @@ struct TcChunks {
   int nrhs;
 };
 
+// Two stages in one launch: block (b, slot) adds the partials of its contiguous
+// range of CTAs in a fixed order and stores the sum in place of the range's first
+// partial (which only this block reads); the last block of the slot to finish
+// (atomic ticket) adds the EPI_FIN_BLOCKS range sums in index order and runs the
+// finaliser.  The result does not depend on timing.  A single block per slot
+// summing every partial (65,536 of them at 32^3x64) took about 70 us.
+constexpr int EPI_FIN_BLOCKS = 64;
+
 template <int EPI>
-__global__ void __launch_bounds__(1024) tc_epi_finalize_kernel(const double* __restrict__ partials, int maxch,
-                                                               TcChunks ch, const int* __restrict__ active,
-                                                               Scalars* sc) {
-  const int slot = blockIdx.x;
+__global__ void __launch_bounds__(256) tc_epi_finalize_kernel(double* __restrict__ partials, int maxch, TcChunks ch,
+                                                              const int* __restrict__ active,
+                                                              unsigned* __restrict__ counters, Scalars* sc) {
+  const int slot = blockIdx.y, b = blockIdx.x;
   if (active && !active[slot]) return;
   const int n = ch.nch[slot / ch.nrhs];
-  const double* part = partials + (size_t)slot * maxch * 3;
-  // four independent partial sums per thread keep four loads in flight (fixed order:
-  // the result does not depend on timing)
-  double acc[4][3] = {};
-  for (int c0 = threadIdx.x; c0 < n; c0 += 4 * blockDim.x) {
-    double v[4][3];
+  const int per = (n + EPI_FIN_BLOCKS - 1) / EPI_FIN_BLOCKS;
+  const int c_lo = b * per, c_hi = min(n, c_lo + per);
+  double* part = partials + (size_t)slot * maxch * 3;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int c = c_lo + (int)threadIdx.x; c < c_hi; c += blockDim.x) {
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int c = c0 + u * blockDim.x;
-#pragma unroll
-      for (int k = 0; k < 3; k++) v[u][k] = c < n ? part[(size_t)c * 3 + k] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++)
-#pragma unroll
-      for (int k = 0; k < 3; k++) acc[u][k] += v[u][k];
+    for (int k = 0; k < 3; k++) acc[k] += __ldcg(part + (size_t)c * 3 + k);
   }
-  __shared__ double sh[3][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double sh[3][8];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
   for (int k = 0; k < 3; k++) {
-    double v = warp_sum((acc[0][k] + acc[1][k]) + (acc[2][k] + acc[3][k]));
+    const double v = warp_sum(acc[k]);
     if (lane == 0) sh[k][warp] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[3];
-    for (int k = 0; k < 3; k++) {
-      tot[k] = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot[k] += sh[k][w];
+    if (c_lo < c_hi) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        double v = 0.0;
+        for (int w = 0; w < nw; w++) v += sh[k][w];
+        part[(size_t)c_lo * 3 + k] = v;
+      }
     }
-    epi_finalize<EPI>(sc[slot], tot);
+    __threadfence();
+    const unsigned ticket = atomicAdd(&counters[slot], 1u);
+    last = (ticket == (unsigned)gridDim.x - 1u);
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot[3] = {0.0, 0.0, 0.0};
+  for (int bb = 0; bb < (int)gridDim.x; bb++) {
+    const int c = bb * per;
+    if (c >= n) break;
+#pragma unroll
+    for (int k = 0; k < 3; k++) tot[k] += __ldcg(part + (size_t)c * 3 + k);
+  }
+  epi_finalize<EPI>(sc[slot], tot);
+  counters[slot] = 0u;
 }
 
 inline cudaError_t launch_epi_finalize(int epi, const DslashArgs& a, cudaStream_t st) {
   TcChunks ch;
   ch.nrhs = a.nrhs_tc;
   for (int l = 0; l < MAXLAT; l++) ch.nch[l] = l < a.b.nlat ? a.b.lat[l].nchunk : 0;
-  const int nslot = a.b.nlat * a.nrhs_tc;
+  const dim3 grid(EPI_FIN_BLOCKS, a.b.nlat * a.nrhs_tc);
   switch (epi) {
-    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
-    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<nslot, 1024, 0, st>>>(a.partials, a.maxch, ch, a.active, a.sc); break;
+    case EPI_ALPHA: tc_epi_finalize_kernel<EPI_ALPHA><<<grid, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.counters, a.sc); break;
+    case EPI_OMEGA: tc_epi_finalize_kernel<EPI_OMEGA><<<grid, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.counters, a.sc); break;
+    case EPI_CGALPHA: tc_epi_finalize_kernel<EPI_CGALPHA><<<grid, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.counters, a.sc); break;
+    case EPI_CGZ: tc_epi_finalize_kernel<EPI_CGZ><<<grid, 256, 0, st>>>(a.partials, a.maxch, ch, a.active, a.counters, a.sc); break;
     default: return cudaSuccess;
   }
   return cudaGetLastError();
@@ -1024,7 +1057,8 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes) {
     } else if (pf)                                                                              \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 16, false, true><<<a.b.total_blocks, threads, 0, st>>>(a); \
     else if (ts == 32)                                                                          \
-      dslash_mrhs_kernel<P, DAG, MODE, EPI, 32><<<a.b.total_blocks, threads, 0, st>>>(a);       \
+      dslash_mrhs_kernel<P, DAG, MODE, EPI, 32>                                                 \
+          <<<dim3(a.b.total_blocks, (a.nrhs_tc + MR32_RPC - 1) / MR32_RPC), 32 * std::min(a.nrhs_tc, MR32_RPC), 0, st>>>(a); \
     else if (ts == 8)                                                                           \
       dslash_mrhs_kernel<P, DAG, MODE, EPI, 8><<<a.b.total_blocks, threads, 0, st>>>(a);        \
     else                                                                                        \

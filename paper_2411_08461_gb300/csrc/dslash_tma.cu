@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256, 4)
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
   const LatGeom& g = a.b.lat[0];
+  const R alpha = R(a.alpha[0]), beta = R(a.beta[0]);
   const int nrhs = a.nrhs_tc;
   const int p = a.out_parity;
   const long stride = g.stride;
@@ -156,20 +157,25 @@ __global__ void __launch_bounds__(256, 4)
       u[1][1] = {q2.x, q2.y};
       u[1][2] = {q2.z, q2.w};
       reconstruct_row2(u);
+      // the factors shared by all RHS, folded in as in dslash_mrhs_kernel: alpha into the
+      // links (XPAY) or the clover term (POST), the t-hop weights into the t links
+      R f = (MODE & MODE_POST) ? R(1) : alpha;
+      if (d >= 6) f = f * hop_t_weight<R>(g, (Tb[ls] & (d == 6 ? 1 : 2)) != 0);
 #pragma unroll
       for (int k = 0; k < 9; k++) {
-        Us[d][ls][2 * k] = u[k / 3][k % 3].re;
-        Us[d][ls][2 * k + 1] = u[k / 3][k % 3].im;
+        Us[d][ls][2 * k] = f * u[k / 3][k % 3].re;
+        Us[d][ls][2 * k + 1] = f * u[k / 3][k % 3].im;
       }
     }
     const float4* cs = rs + (TMA_FWD_BYTES + 4 * TMA_BWD_BYTES) / 16;
+    const R cf = (MODE & MODE_POST) ? alpha : beta;  // beta: the clover term applied to x
     for (int e = threadIdx.x; e < 18 * TMA_TS; e += blockDim.x) {
       const int ls = e % TMA_TS, k = e / TMA_TS;
       const float4 v = cs[k * TMA_TS + ls];
-      Cs[ls][4 * k] = v.x;
-      Cs[ls][4 * k + 1] = v.y;
-      Cs[ls][4 * k + 2] = v.z;
-      Cs[ls][4 * k + 3] = v.w;
+      Cs[ls][4 * k] = cf * v.x;
+      Cs[ls][4 * k + 1] = cf * v.y;
+      Cs[ls][4 * k + 2] = cf * v.z;
+      Cs[ls][4 * k + 3] = cf * v.w;
     }
     __syncthreads();
     // compute: thread = (site ls, rhs), as in dslash_mrhs_kernel
@@ -182,22 +188,16 @@ __global__ void __launch_bounds__(256, 4)
       cpx<R> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
-      const int tb = Tb[ls];
-      const R sf = hop_t_weight<R>(g, tb & 1);
-      const R sb = hop_t_weight<R>(g, tb & 2);
+      const R sf = R(1), sb = R(1);  // in the staged t links
       hop_dir_smem<F32, 0, DAG>(acc, in, nullptr, stride, Nb[0][ls], Nb[1][ls], Us[0][ls], Us[1][ls], R(1), R(1));
       hop_dir_smem<F32, 1, DAG>(acc, in, nullptr, stride, Nb[2][ls], Nb[3][ls], Us[2][ls], Us[3][ls], R(1), R(1));
       hop_dir_smem<F32, 2, DAG>(acc, in, nullptr, stride, Nb[4][ls], Nb[5][ls], Us[4][ls], Us[5][ls], R(1), R(1));
       hop_dir_smem<F32, 3, DAG>(acc, in, nullptr, stride, Nb[6][ls], Nb[7][ls], Us[6][ls], Us[7][ls], sf, sb);
-      const R alpha = R(a.alpha[0]);
-#pragma unroll
-      for (int k = 0; k < 12; k++) acc[k] = alpha * acc[k];
       if (MODE & MODE_XPAY) {
         cpx<R> xv[12];
         SpinorIO<F32>::load_cs(xv, rhs_ptr<F32>(a.x, 0, rhs, stride), nullptr, stride, i);
-        const R beta = R(a.beta[0]);
-        hermitian6_axpy_row(acc, beta, Cs[ls], xv);
-        hermitian6_axpy_row(acc + 6, beta, Cs[ls] + 36, xv + 6);
+        hermitian6_axpy_row(acc, R(1), Cs[ls], xv);
+        hermitian6_axpy_row(acc + 6, R(1), Cs[ls] + 36, xv + 6);
         if (EPI == EPI_ALPHA) {
           cpx<R> fv[12];
           SpinorIO<F32>::load_cs(fv, rhs_ptr<F32>(a.f, 0, rhs, stride), nullptr, stride, i);

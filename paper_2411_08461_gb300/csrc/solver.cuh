@@ -480,15 +480,18 @@ struct KrylovSolver {
       count_launch(c0);
     }
     // b_hat = b_e + kappa D_eo A_oo^-1 b_o
-    // (double-float operator: b_hat only seeds the iteration; every reported
-    // residual is evaluated from b itself in FP64)
-    if (use_df) {
-      // b_e's double-float copy goes to r64 and b_hat's to x_o (both free until the first update)
-      WCL_CHECK(convert(ctxs, DF64, F64, nrhs, bo_df, b_o, nullptr));
-      WCL_CHECK(convert(ctxs, DF64, F64, nrhs, r64, b_e, nullptr));
-      WCL_CHECK(clover_apply(ctxs, DF64, nrhs, tmp64, bo_df, 1, CL_AINV, nullptr));
-      WCL_CHECK(dslash(ctxs, DF64, nrhs, x_o, tmp64, &r64, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
-      WCL_CHECK(convert(ctxs, F64, DF64, nrhs, bhat, x_o, nullptr));
+    // In a mixed-precision solve b_hat only seeds the iteration: the first
+    // residual replacement evaluates b_e - (M x)_e from b itself, with x_o
+    // rebuilt from b_o, so every later residual and every reported one is
+    // independent of how b_hat was rounded.  It is therefore formed with the
+    // sloppy operator (v, t, tmp and r are free until the first iteration).
+    if (use_df) WCL_CHECK(convert(ctxs, DF64, F64, nrhs, bo_df, b_o, nullptr));
+    if (S != F64) {
+      WCL_CHECK(convert(ctxs, S, F64, nrhs, v, b_o, nullptr));
+      WCL_CHECK(convert(ctxs, S, F64, nrhs, t, b_e, nullptr));
+      WCL_CHECK(clover_apply(ctxs, S, nrhs, tmp, v, 1, CL_AINV, nullptr));
+      WCL_CHECK(dslash(ctxs, S, nrhs, r, tmp, &t, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
+      WCL_CHECK(convert(ctxs, F64, S, nrhs, bhat, r, nullptr));
     } else {
       WCL_CHECK(clover_apply(ctxs, F64, nrhs, tmp64, b_o, 1, CL_AINV, nullptr));
       WCL_CHECK(dslash(ctxs, F64, nrhs, bhat, tmp64, &b_e, 0, false, CL_NONE, CL_NONE, C_KAPPA, C_ONE, nullptr));
