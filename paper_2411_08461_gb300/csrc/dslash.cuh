@@ -541,6 +541,73 @@ __device__ __forceinline__ void link_mul_row(const R* row, const cpx<R> h[6], cp
   for (int k = 0; k < 6; k++) o[k] = sign * o[k];
 }
 
+// A gathered neighbour spinor as it arrives from memory.  The 16-bit formats keep their
+// packed halves and the site's norm; they are unpacked only when the hop is computed,
+// and the norm is applied to the hop's link-multiply output (12 reals) instead of to
+// the spinor (24 reals): the projection and the link multiply are linear.
+template <int P>
+struct RawSpinor {  // FP32: six 16-byte chunks
+  float4 c[6];
+};
+template <>
+struct RawSpinor<F64> {
+  double2 c[12];
+};
+struct RawSpinor16 {
+  uint4 c[3];
+  float n;
+};
+template <>
+struct RawSpinor<F16> : RawSpinor16 {};
+template <>
+struct RawSpinor<BF16> : RawSpinor16 {};
+
+template <int P>
+__device__ __forceinline__ void load_raw(RawSpinor<P>& r, const void* base, const float* norm, long stride, long j) {
+  if constexpr (P == F64) {
+    const double2* q = static_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) r.c[k] = ldg(q + k * stride + j);
+  } else if constexpr (P == F32) {
+    const float4* q = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; k++) r.c[k] = ldg(q + k * stride + j);
+  } else {
+    const uint4* q = static_cast<const uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; k++) r.c[k] = ldg(q + k * stride + j);
+    r.n = ldg(norm + j);
+  }
+}
+
+// unpack without the norm; returns the factor still to be applied (1, or the norm)
+template <int P>
+__device__ __forceinline__ typename Traits<P>::R unpack_raw(const RawSpinor<P>& r, cpx<typename Traits<P>::R> v[12]) {
+  if constexpr (P == F64) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) v[k] = {r.c[k].x, r.c[k].y};
+    return 1.0;
+  } else if constexpr (P == F32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      v[2 * k] = {r.c[k].x, r.c[k].y};
+      v[2 * k + 1] = {r.c[k].z, r.c[k].w};
+    }
+    return 1.f;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint32_t w[4] = {r.c[k].x, r.c[k].y, r.c[k].z, r.c[k].w};
+#pragma unroll
+      for (int m = 0; m < 4; m++) {
+        const float2 f = unpack2<P>(w[m]);
+        v[4 * k + m] = {f.x, f.y};
+      }
+    }
+    return r.n;
+  }
+}
+
 // U_f, U_b: shared-memory rows of the forward link at the site and the backward
 // link at the neighbour (18 reals each)
 template <int P, int MU, bool DAG>
@@ -552,13 +619,16 @@ __device__ __forceinline__ void hop_dir_smem(cpx<typename Traits<P>::R> acc[12],
   constexpr int SF = DAG ? +1 : -1;
   constexpr int SB = -SF;
   cpx<R> psi[12], h[6], uh[6];
-  SpinorIO<P>::load(psi, in, in_norm, stride, jf);
+  RawSpinor<P> raw;
+  load_raw<P>(raw, in, in_norm, stride, jf);
+  R nf = unpack_raw<P>(raw, psi);
   project<MU, SF>(psi, h);
-  link_mul_row<false>(U_f, h, uh, sf);
+  link_mul_row<false>(U_f, h, uh, sf * nf);
   reconstruct_acc<MU, SF>(acc, uh);
-  SpinorIO<P>::load(psi, in, in_norm, stride, jb);
+  load_raw<P>(raw, in, in_norm, stride, jb);
+  nf = unpack_raw<P>(raw, psi);
   project<MU, SB>(psi, h);
-  link_mul_row<true>(U_b, h, uh, sb);
+  link_mul_row<true>(U_b, h, uh, sb * nf);
   reconstruct_acc<MU, SB>(acc, uh);
 }
 
@@ -719,13 +789,15 @@ struct MrhsBounds<32> {
 // ASYNC: the eight neighbour spinors of a thread are staged through shared memory
 // with cp.async, two hops in flight (dynamic shared memory: 2 stages x CH chunks x
 // blockDim 16-byte slots, plus norms)
-// PF: the neighbour spinor of the next hop is loaded into registers before the current
-// hop is computed (software pipelining: one hop's gathers always in flight), with the
-// register cap of the staged variant
+// PF: the neighbour spinor of the next hop is loaded into registers, as it arrives
+// from memory (packed for the 16-bit formats), before the current hop is computed
+// (software pipelining: one hop's gathers always in flight); FP32 and FP64 with the
+// register cap of the staged variant, the 16-bit formats (13 registers in flight) with
+// that of the plain kernel
 template <int P, bool DAG, int MODE, int EPI, int TS, bool ASYNC = false, bool PF = false>
 __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
-                                  (P == F64 ? 1 : (ASYNC || PF) ? MrhsBounds<TS>::MIN_BLOCKS - 1
-                                                                : MrhsBounds<TS>::MIN_BLOCKS))
+                                  (P == F64 ? 1 : (ASYNC || (PF && P == F32)) ? MrhsBounds<TS>::MIN_BLOCKS - 1
+                                                                               : MrhsBounds<TS>::MIN_BLOCKS))
     dslash_mrhs_kernel(const __grid_constant__ DslashArgs a) {
   using R = typename Traits<P>::R;
   constexpr bool CLOV = (MODE & MODE_POST) || (MODE & MODE_PRE);
@@ -878,15 +950,15 @@ __global__ void __launch_bounds__(MrhsBounds<TS>::THREADS,
         }
       }
     } else if constexpr (PF) {
-      cpx<R> nxt[12];
-      SpinorIO<P>::load(nxt, in, in_norm, stride, Nb[0][ls]);
+      RawSpinor<P> nxt;
+      load_raw<P>(nxt, in, in_norm, stride, Nb[0][ls]);
 #pragma unroll
       for (int hh = 0; hh < 8; hh++) {
+        const RawSpinor<P> cur = nxt;
+        if (hh < 7) load_raw<P>(nxt, in, in_norm, stride, Nb[hh + 1][ls]);
         cpx<R> psi[12];
-#pragma unroll
-        for (int k = 0; k < 12; k++) psi[k] = nxt[k];
-        if (hh < 7) SpinorIO<P>::load(nxt, in, in_norm, stride, Nb[hh + 1][ls]);
-        const R sign = hh == 6 ? sf : hh == 7 ? sb : R(1);
+        const R sc = unpack_raw<P>(cur, psi);
+        const R sign = (hh == 6 ? sf : hh == 7 ? sb : R(1)) * sc;
         switch (hh) {
           case 0: hop_from<0, false, DAG>(acc, psi, Us[0][ls], sign); break;
           case 1: hop_from<0, true, DAG>(acc, psi, Us[1][ls], sign); break;
