@@ -45,8 +45,8 @@ FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 vector rate, nominal
 # averaged over the solve's launch mix (2 x A^-1 D x, 1 x alpha-fused, 1 x omega-fused), from
 # one ncu capture of 8 such launches of the same solve on 32^3x16 -- the bench lattice's
 # spatial volume, so the t neighbours lie as far apart as at 32^3x64, with a few GB on the
-# device: 978/1158/943/1472 MB per launch for 3.15 M site-RHS, 361.7 B against 320 algorithmic
-TRAFFIC_F32_12RHS_PER_SITE_RHS = 361.7
+# device: 998/1145/967/1455 MB per launch for 3.15 M site-RHS, 362.8 B against 320 algorithmic
+TRAFFIC_F32_12RHS_PER_SITE_RHS = 362.8
 UNIT = "12-RHS solves/s"
 WORKLOAD = "32^3x64 Wilson-clover, eps 0.3, kappa 0.1235, c_sw 1.0, 12 spin-colour point sources, tol 1e-10"
 
@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--kappa", type=float, default=KAPPA, help="hopping parameter of --case mg")
     ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
     ap.add_argument("--mg-nvec", type=int, default=24, help="--case mg: null vectors")
+    ap.add_argument("--mg-coarse-steps", type=int, default=8,
+                    help="--case mg: coarse GCR steps of the batched K-cycle (solver fgcr_mg_batched)")
+    ap.add_argument("--mg-single", type=int, default=1,
+                    help="--case mg: also time the one-right-hand-side-at-a-time multigrid FGCR")
     ap.add_argument("--lattice", default="24,24,24,48", help="lattice of --case mhat")
     ap.add_argument("--dims", default="32,32,32,64", help="lattice of --case solve (the bench line uses 32^3x64)")
     ap.add_argument("--nrhs", type=int, default=12, help="right-hand sides of --case mhat")
@@ -435,7 +439,7 @@ def run_ours(args, rank, world, local):
                      "avg_launch_ms": s_ms / max(1, s_n),
                      "traffic": traffic,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of 8 launches of this "
-                                       "kernel in the same solve on 32^3x16 (361.7 B per site-RHS against 320 "
+                                       "kernel in the same solve on 32^3x16 (362.8 B per site-RHS against 320 "
                                        "algorithmic, 1.13x), scaled by the site-RHS of one launch here",
                      "gflops": s_flops / (s_ms * 1e-3) / 1e9 if s_ms > 0 else None,
                      "share_of_profiled_solve": s_ms / max(1e-9, pinfos[0]["seconds"] * 1e3)},
@@ -1006,21 +1010,39 @@ def run_mg_case(args):
     ctx.wcl_mg_setup(starts, mprm)  # warm-up (tuner, module loading)
     setup_s, _ = timed(lambda: ctx.wcl_mg_setup(starts, mprm))
     del starts
-    mg = pkg.wcl_default_params(solver="fgcr_mg", tol=args.tol, gcr_nkrylov=20)
-    ctx.wcl_invert(x[:1], src[:1], 1, mg)  # warm-up
-    mg_s, infos = timed(lambda: ctx.wcl_invert(x, src, 12, mg)[1])
+    line = {"case": "mg", "lattice": dims, "kappa": args.kappa, "block": block, "nvec": args.mg_nvec,
+            "relax_steps": mprm.relax_steps, "setup_seconds": setup_s}
+    if args.mg_single:
+        mg = pkg.wcl_default_params(solver="fgcr_mg", tol=args.tol, gcr_nkrylov=20)
+        ctx.wcl_invert(x[:1], src[:1], 1, mg)  # warm-up
+        mg_s, infos = timed(lambda: ctx.wcl_invert(x, src, 12, mg)[1])
+        line["mg_fgcr"] = {"seconds": mg_s, "outer_iters_per_rhs": float(np.mean([i["iters"] for i in infos])),
+                           "restarts_per_rhs": float(np.mean([i["reliable_updates"] for i in infos])),
+                           "worst_true_residual": max(i["true_residual"] for i in infos)}
+    # all twelve right-hand sides at once: FGCR on M_hat with the batched K-cycle (fixed
+    # coarse steps, every coefficient on the device)
+    starts = torch.from_numpy(W.gaussian_fermion(dims, 500, nrhs=args.mg_nvec)).to(dev)
+    bprm = pkg.wcl_default_mg_params(block=block, nvec=args.mg_nvec, coarse_maxiter=args.mg_coarse_steps)
+    ctx.wcl_mg_setup(starts, bprm)
+    del starts
+    mgb = pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=args.tol, gcr_nkrylov=20,
+                                 delta_reliable=3e-4)
+    ctx.wcl_invert(x, src, 12, mgb)  # warm-up (tuner, workspace)
+    mgb_s, binf = timed(lambda: ctx.wcl_invert(x, src, 12, mgb)[1])
+    line["mg_fgcr_batched"] = {"seconds": mgb_s, "coarse_steps": args.mg_coarse_steps,
+                               "outer_iters_per_rhs": float(np.mean([i["iters"] for i in binf])),
+                               "reliable_updates_per_rhs": float(np.mean([i["reliable_updates"] for i in binf])),
+                               "worst_true_residual": max(i["true_residual"] for i in binf)}
     bi = pkg.wcl_default_params(solver="bicgstab", sloppy="f32", tol=args.tol, check_every=2, delta_reliable=3e-4)
     ctx.wcl_invert(x, src, 12, bi)
     bi_s, binfos = timed(lambda: ctx.wcl_invert(x, src, 12, bi)[1])
-    print(json.dumps({"case": "mg", "lattice": dims, "kappa": args.kappa, "block": block, "nvec": args.mg_nvec,
-                      "relax_steps": mprm.relax_steps, "setup_seconds": setup_s,
-                      "mg_fgcr": {"seconds": mg_s, "outer_iters_per_rhs": float(np.mean([i["iters"] for i in infos])),
-                                  "restarts_per_rhs": float(np.mean([i["reliable_updates"] for i in infos])),
-                                  "worst_true_residual": max(i["true_residual"] for i in infos)},
-                      "batched_bicgstab_f32": {"seconds": bi_s,
-                                               "iters_per_rhs": float(np.mean([i["iters"] for i in binfos])),
-                                               "worst_true_residual": max(i["true_residual"] for i in binfos)},
-                      "mg_over_bicgstab_time": (mg_s + setup_s) / bi_s}))
+    line["batched_bicgstab_f32"] = {"seconds": bi_s, "iters_per_rhs": float(np.mean([i["iters"] for i in binfos])),
+                                    "worst_true_residual": max(i["true_residual"] for i in binfos)}
+    if args.mg_single:
+        line["mg_over_bicgstab_time"] = (line["mg_fgcr"]["seconds"] + setup_s) / bi_s
+    line["mg_batched_over_bicgstab_time"] = mgb_s / bi_s
+    line["mg_batched_with_setup_over_bicgstab_time"] = (mgb_s + setup_s) / bi_s
+    print(json.dumps(line))
     ctx.close()
     return 0
 
