@@ -6,11 +6,12 @@ import pytest
 
 import test_oracle_contract as TC
 import test_oracle_dirac as TD
+import test_oracle_force as TF
 import test_oracle_hisq as THQ
 import test_oracle_multigrid as TM
 import test_oracle_ptc as TP
 import test_oracle_solvers as TS
-from oracle import contract, dirac, hisq, multigrid, ptc, solvers
+from oracle import contract, dirac, force, hisq, multigrid, ptc, solvers
 from oracle import lattice as L
 
 
@@ -280,3 +281,34 @@ def test_hisq_naik_shifted(monkeypatch):
     monkeypatch.setattr(hisq, "naik", bad)
     _fails(THQ.test_naik_link_paths)
     _fails(THQ.test_hisq_links_gauge_covariance)
+
+
+def test_force_leaf_offset(monkeypatch):
+    """Clover force: the third factor of the first leaf credited one site off in mu."""
+    bad = list(force.LEAVES)
+    bad[0] = (bad[0][0], bad[0][1], (0, True, (1, 1)), bad[0][3])
+    monkeypatch.setattr(force, "LEAVES", tuple(bad))
+    _fails(TF.test_single_link_variations, -1)
+
+
+def test_force_odd_trace_without_kappa2(monkeypatch):
+    """Clover force: the odd sites' sigma trace without its kappa^2."""
+    orig = force.sigma_trace
+    calls = []
+
+    def bad(a, b):
+        calls.append(1)
+        lam = orig(a, b)
+        if len(calls) % 2 == 0:  # the second call of each force is the odd pair (W, Z)
+            lam = {k: v / (0.12 * 0.12) for k, v in lam.items()}
+        return lam
+
+    monkeypatch.setattr(force, "sigma_trace", bad)
+    _fails(TF.test_force_is_the_derivative_of_the_action, (2, 2, 2, 2), False)
+
+
+def test_force_determinant_sign(monkeypatch):
+    """Clover force: + 2 log det A_oo instead of - 2 log det A_oo."""
+    orig = force.logdet_trace
+    monkeypatch.setattr(force, "logdet_trace", lambda ainv: {k: -v for k, v in orig(ainv).items()})
+    _fails(TF.test_determinant_term_alone)
