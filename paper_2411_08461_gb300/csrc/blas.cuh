@@ -344,10 +344,13 @@ struct BicgUpdate {  // x += alpha p + omega s; r = s - omega t; then rho' and |
     const double2 a2 = sc[s.slot].alpha, o2 = sc[s.slot].omega;
     cpx<R> pp[12], ss[12], tt[12], rh[12];
     cpx<RX> xx[12];
+    // every load is issued before the first store: the stores go through pointers the
+    // compiler cannot separate from rhat, so a later load would wait for them
     WCL_LD(S, true, pp, p);
     WCL_LD(S, false, ss, r);
     WCL_LD(S, true, tt, t);
     WCL_LD(X, false, xx, xs);
+    WCL_LD(S, true, rh, rhat);
     const cpx<RX> ax = {RX(a2.x), RX(a2.y)}, ox = {RX(o2.x), RX(o2.y)};
     const cpx<R> om = to_c<R>(o2);
 #pragma unroll
@@ -358,7 +361,6 @@ struct BicgUpdate {  // x += alpha p + omega s; r = s - omega t; then rho' and |
     }
     WCL_ST(X, xx, xs);
     WCL_ST(S, ss, r);
-    WCL_LD(S, true, rh, rhat);
     dot_acc(acc, rh, ss);
     acc[2] += norm_site(ss);
   }
@@ -381,12 +383,15 @@ __device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void*
 }
 
 // Reliable update: r64 holds y = A_ee x_e - kappa D_eo x_o in precision Q (x_o the
-// reconstructed odd solution) and is overwritten, in place, by the FP64 residual
-// r_e = b_e - y, which equals the Schur residual b_hat - M_hat x_e; rS = r_e in the
-// inner precision.  ro, when given, holds the odd residual b_o - (A_oo x_o - kappa
-// D_oe x_e) of the reconstruction (precision Q).  aux[0] = ||r_e||^2, aux[3] =
-// ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true residual); BiCGStab also
-// recomputes rho against rhat (REPLACE).
+// reconstructed odd solution); r_e = b_e - y is formed in FP64 and equals the Schur
+// residual b_hat - M_hat x_e; rS = r_e in the inner precision.  ro, when given, holds
+// the odd residual b_o - (A_oo x_o - kappa D_oe x_e) of the reconstruction (precision
+// Q).  aux[0] = ||r_e||^2, aux[3] = ||r_e||^2 + ||r_o||^2 = ||b - M x||^2 (the full true
+// residual); BiCGStab also recomputes rho against rhat (REPLACE).  The sums of an IEEE
+// FP64 update (Q = F64: every update that may end a solve) are FP64 throughout; those
+// of a double-float update, which only decide whether an FP64 update follows, sum the
+// residual as rounded to the inner precision per site (FP32 pipes; GB300's FP64 rate
+// bounded this kernel) and add the per-site sums in FP64.
 template <int S, int Q>
 struct ResidualReplace {
   FieldRef r64, bhat, rS, rhat, ro;
@@ -394,6 +399,8 @@ struct ResidualReplace {
   __device__ void operator()(const Slice& s, const LatGeom& g, long i, double* acc) const {
     using R = typename Traits<S>::R;
     cpx<double> y[12], b[12];
+    cpx<R> rh[12];
+    if (bicg) WCL_LD(S, true, rh, rhat);
     if (ro.ptr[s.l]) {  // odd residual of the reconstruction (absent: x_o solves its rows exactly)
       load_as_f64<Q>(b, rhs_ptr<Q>(ro, s.l, s.rhs, g.stride), g.stride, i);
       acc[3] += norm_site(b);
@@ -406,19 +413,26 @@ struct ResidualReplace {
       y[k] = b[k] - y[k];
       rs[k] = {R(y[k].re), R(y[k].im)};
     }
-    WCL_ST(F64, y, r64);
     WCL_ST(S, rs, rS);
-    acc[0] += norm_site(y);
-    if (bicg) {
-      cpx<R> rh[12];
-      WCL_LD(S, true, rh, rhat);
-      cpx<double> rhd[12];
+    if constexpr (Q == F64) {
+      acc[0] += norm_site(y);
+      if (bicg) {
+        cpx<double> rhd[12];
 #pragma unroll
-      for (int k = 0; k < 12; k++) rhd[k] = {double(rh[k].re), double(rh[k].im)};
-      double d[2] = {0, 0};
-      dot_acc(d, rhd, y);
-      acc[1] += d[0];
-      acc[2] += d[1];
+        for (int k = 0; k < 12; k++) rhd[k] = {double(rh[k].re), double(rh[k].im)};
+        double d[2] = {0, 0};
+        dot_acc(d, rhd, y);
+        acc[1] += d[0];
+        acc[2] += d[1];
+      }
+    } else {
+      acc[0] += norm_site(rs);
+      if (bicg) {
+        double d[2] = {0, 0};
+        dot_acc(d, rh, rs);
+        acc[1] += d[0];
+        acc[2] += d[1];
+      }
     }
   }
   __device__ void finalize(Scalars& c, const double* t) const {
