@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
     ap.add_argument("--case", default="solve",
                     choices=["solve", "mhat", "compare", "batch", "throughput", "precond", "propagator", "mg",
-                             "staggered"],
+                             "staggered", "force"],
                     help="mhat: only apply the Schur operator (the small case used for ncu captures); "
                          "batch: four uneven lattices x 12 Z2 sources in one batched solve vs single-RHS "
                          "solves; throughput: 16^3x32 FP32 operator applies and one point-source solve; "
@@ -73,7 +73,8 @@ def parse():
                          "two- and three-point functions) on --dims, with the contraction kernel's roofline; "
                          "mg: the two-level multigrid (setup, then FGCR-MG on the 12 point sources) against "
                          "the batched BiCGStab solve on --dims at --kappa; staggered: the HISQ-form staggered "
-                         "operator on --dims (FP64 and FP32 applies, GB/s) and its even-odd CG solve")
+                         "operator on --dims (FP64 and FP32 applies, GB/s) and its even-odd CG solve; force: "
+                         "the FP64 clover fermion force (HMC) on --dims")
     ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of --case propagator / mg")
     ap.add_argument("--kappa", type=float, default=KAPPA, help="hopping parameter of --case mg")
     ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
@@ -1047,6 +1048,54 @@ def run_mg_case(args):
     return 0
 
 
+def run_force_case(args):
+    """FP64 clover fermion force of the two-flavour even-odd action on --dims (kappa
+    0.1235, c_sw 1, clover determinant term included) for a Gaussian X, timed through
+    wcl_clover_force with CUDA events (the call applies M_hat and two FP64 half-dslashes,
+    then the per-site Omega kernel and the per-link force kernel).  FP64 flops counted
+    per link (hopping outer products 1.4 k, 24 clover-leaf terms of four 3x3 complex
+    products 21 k, U G and the projection 0.3 k) and per site (the sigma traces and the
+    determinant term 7.9 k), against the FP64 nominal rate."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2411_08461_gb300 as pkg
+
+    dims = tuple(int(v) for v in args.dims.split(","))
+    vol = dims[0] * dims[1] * dims[2] * dims[3]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pkg.Context(dims, stream=stream)
+    gauge = torch.from_numpy(W.gauge_links(dims, EPS, SEED)).to(dev)
+    ctx.wcl_load_gauge(gauge, KAPPA, CSW)
+    x = torch.from_numpy(np.ascontiguousarray(W.gaussian_fermion(dims, 1)[0])).to(dev)
+    out = torch.empty_like(gauge)
+    ctx.wcl_clover_force(out, x, True)  # warm-up (work space, module load)
+    torch.cuda.synchronize()
+    runs = []
+    for _ in range(max(1, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.wcl_clover_force(out, x, True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        runs.append(a.elapsed_time(b))
+    ms = statistics.median(runs)
+    flops = 4 * vol * (1.44e3 + 21.1e3 + 0.3e3) + vol * 7.9e3 + 4 * (vol // 2) * 1824
+    line = {"case": "force", "lattice": dims, "ms": ms, "runs": len(runs),
+            "fp64_gflop": flops / 1e9, "fp64_tflops": flops / (ms * 1e-3) / 1e12, "fp64_nominal_tflops": 1.25,
+            "frac_of_nominal": flops / (ms * 1e-3) / 1e12 / 1.25,
+            "what": "wcl_clover_force, FP64, two-flavour even-odd clover action with the odd clover determinant"}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.case == "mhat":
@@ -1065,6 +1114,8 @@ def main():
         return run_mg_case(args)
     if args.case == "staggered":
         return run_staggered_case(args)
+    if args.case == "force":
+        return run_force_case(args)
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores only; other ranks exit without work
         return run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))

@@ -519,6 +519,21 @@ wcl_status wcl_apply_staggered(wcl_ctx* ctx, void* d_out, const void* d_in, wcl_
 wcl_status wcl_invert_staggered(wcl_ctx* ctx, void* d_x, const void* d_b, int nrhs, const wcl_solve_params* params,
                                 wcl_solve_info* info);
 
+/* ---- clover fermion force (Sec. IV: the paper's HMC uses the clover and HISQ forces) ----
+ * F = the force of the two-flavour even-odd clover action of ctx's (isotropic) operator,
+ *   S(U) = phi^+ (M_hat^+ M_hat)^-1 phi - 2 sum_{x odd} log det A(x),
+ * the second term (the clover determinant of the odd sites) only with include_logdet != 0.
+ * d_x_e: X = (M_hat^+ M_hat)^-1 phi on the even sites ([Lt][Lz][Ly][Lx/2][4][3]
+ * complex128, the caller's solve; the force is evaluated for whatever X is given).
+ * d_force: [4][2][Lt][Lz][Ly][Lx/2][3][3] complex128 (the QDP gauge layout), receives
+ * F_mu(x), traceless anti-Hermitian, defined by dS/d eps = -Tr(Q F_mu(x)) for the left
+ * variation U_mu(x) -> exp(eps Q) U_mu(x) (Q traceless anti-Hermitian); an HMC step then
+ * moves the momenta by -dt F.  Both buffers device memory of ctx's GPU or page-locked host
+ * memory, caller-owned.  FP64 throughout (links, clover inverse and operator of ctx).
+ * Errors: WCL_ERR_NO_GAUGE; WCL_ERR_INVALID_ARG (null or foreign pointer, or a context
+ * loaded with wcl_load_gauge_aniso); WCL_ERR_NONFINITE (non-finite X); WCL_ERR_CUDA. */
+wcl_status wcl_clover_force(wcl_ctx* ctx, void* d_force, const void* d_x_e, int include_logdet);
+
 /* Release every library-owned resource of ctx (cf. dirac.destroy, Sec. III.B). */
 wcl_status wcl_destroy(wcl_ctx* ctx);
 

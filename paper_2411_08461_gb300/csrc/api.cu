@@ -250,6 +250,7 @@ static wcl_status load_gauge(wcl_ctx* c, const void* d_gauge, double kappa, doub
   c->lat.loaded = false;
   c->lat.kappa = kappa;
   c->lat.csw = csw_s;
+  c->lat.csw_t = csw_t;
   c->lat.tw = tw;
   WCL_CUDA(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
   WCL_CUDA(import_gauge(c->lat, d_gauge, c->d_flags, c->stream));

@@ -10,6 +10,7 @@ struct LatticeDevice {
   long vh = 0;          // sites per parity
   long stride = 0;      // padded sites per chunk
   double kappa = 0, csw = 0;
+  double csw_t = 0;     // clover coefficient of the planes that contain t (csw: the spatial planes)
   double tw = 1.0;      // t-hop weight: xi_0 / nu of the anisotropic operator (kappa holds kappa nu / xi_0)
   bool loaded = false;
   // [prec][parity], prec = F64, F32, F16, BF16, DF64 (the FP64 values split into float pairs)

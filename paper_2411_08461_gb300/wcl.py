@@ -120,6 +120,7 @@ SIGNATURES = {
     "wcl_contract": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "wcl_destroy": (ctypes.c_int, [_P]),
     "wcl_load_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "wcl_clover_force": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "wcl_hisq_smear": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double]),
     "wcl_apply_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "wcl_invert_staggered": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(wcl_solve_params),
@@ -295,6 +296,16 @@ class Context:
         _check(load_library().wcl_apply_Mpc_noalloc(self.handle, _ptr(out_e, torch.complex128, n, "out_e"),
                                                     _ptr(in_e, torch.complex128, n, "in_e"), int(dagger)),
                "wcl_apply_Mpc_noalloc")
+
+    # ---- clover fermion force ------------------------------------------------------
+    def wcl_clover_force(self, force, x_e, include_logdet: bool = True):
+        """force <- F of the two-flavour even-odd clover action for X = (M_hat^+ M_hat)^-1 phi."""
+        import torch
+
+        _check(load_library().wcl_clover_force(self.handle, _ptr(force, torch.complex128, self.volume * 36, "force", True),
+                                               _ptr(x_e, torch.complex128, self.fermion_numel // 2, "x_e", True),
+                                               int(include_logdet)),
+               "wcl_clover_force")
 
     # ---- staggered operator --------------------------------------------------------
     def wcl_hisq_smear(self, fat, long_links, gauge, eps_naik: float = 0.0):
