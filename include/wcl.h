@@ -88,10 +88,14 @@ typedef enum {
   WCL_CGNR = 1,          /* CG on M_hat^+ M_hat (Sec. II.E: CG) */
   WCL_FGCR_LEARNED = 2,  /* flexible GCR on M_hat with the learned preconditioner */
   WCL_GCR = 3,           /* the same GCR without a preconditioner (the comparison method) */
-  WCL_FGCR_MG = 4        /* flexible GCR on the whole-lattice M preconditioned by the two-level
+  WCL_FGCR_MG = 4,       /* flexible GCR on the whole-lattice M preconditioned by the two-level
                             multigrid K-cycle of wcl_mg_setup (Sec. II.E: QUDA's multigrid), FP32
                             between IEEE FP64 true-residual restarts; right-hand sides one after
                             another, wcl_invert only.  Uses tol, maxiter and gcr_nkrylov. */
+  WCL_FGCR_MG_BATCHED = 5 /* every right-hand side at once: flexible GCR on M_hat (as WCL_GCR, with
+                            its FP64 residual replacements) preconditioned by the batched K-cycle
+                            (wcl_mg_cycle_batched) applied to the even residual with zero odd sites;
+                            sloppy must be WCL_F32; wcl_invert only. */
 } wcl_solver;
 
 typedef struct {
@@ -456,6 +460,14 @@ wcl_status wcl_mg_setup(wcl_ctx* ctx, const void* d_starts, const wcl_mg_params*
 /* d_out = K-cycle(d_in): one application of the preconditioner to a whole-lattice field
  * (QDP fermion, complex128); coarse_iters (may be NULL) receives the coarse GCR steps. */
 wcl_status wcl_mg_cycle(wcl_ctx* ctx, void* d_out, const void* d_in, int* coarse_iters);
+
+/* d_out[r] = K-cycle(d_in[r]) for nrhs whole-lattice QDP fermions (complex128, device or
+ * page-locked host) at once: the steps of wcl_mg_cycle with every minimal-residual and
+ * Gram-Schmidt coefficient computed on the device per right-hand side, the coarse stencil
+ * read once for up to six right-hand sides, and exactly coarse_maxiter coarse GCR steps
+ * (restarted every coarse_nkrylov; coarse_tol is not consulted), so no step waits on the
+ * host.  Allocates its work space on first use.  1 <= nrhs <= 12. */
+wcl_status wcl_mg_cycle_batched(wcl_ctx* ctx, void* d_out, const void* d_in, int nrhs);
 
 /* Restriction P^+ (QDP fermion -> coarse vector) and prolongation P (coarse -> QDP
  * fermion, overwritten); coarse vectors are complex128, device or host memory. */

@@ -421,7 +421,7 @@ static wcl_status check_params(const wcl_solve_params* p) {
     return WCL_ERR_INVALID_ARG;
   }
   if (p->solver != WCL_BICGSTAB && p->solver != WCL_CGNR && p->solver != WCL_FGCR_LEARNED && p->solver != WCL_GCR &&
-      p->solver != WCL_FGCR_MG) {
+      p->solver != WCL_FGCR_MG && p->solver != WCL_FGCR_MG_BATCHED) {
     set_error("unknown solver %d", (int)p->solver);
     return WCL_ERR_INVALID_ARG;
   }
@@ -433,6 +433,16 @@ static wcl_status solve(const std::vector<wcl_ctx*>& v, int nrhs, const wcl_solv
   if (p->solver == WCL_FGCR_LEARNED && !v[0]->ptc.loaded) {
     set_error("learned FGCR: no preconditioner weights loaded (wcl_precond_load / wcl_precond_train)");
     return WCL_ERR_NO_PRECOND;
+  }
+  if (p->solver == WCL_FGCR_MG_BATCHED) {
+    if (p->sloppy != WCL_F32) {
+      set_error("batched multigrid FGCR: sloppy precision must be WCL_F32");
+      return WCL_ERR_INVALID_ARG;
+    }
+    if (!v[0]->mg) {
+      set_error("batched multigrid FGCR: no multigrid hierarchy (wcl_mg_setup)");
+      return WCL_ERR_NO_PRECOND;
+    }
   }
   SolveIO io{d_x, d_b};
   switch (p->sloppy) {
@@ -485,8 +495,8 @@ wcl_status wcl_invert_batch(wcl_ctx* const* ctxs, int nctx, void* const* d_x, co
     return WCL_ERR_INVALID_ARG;
   }
   WCL_CHECK(check_params(params));
-  if (params->solver == WCL_FGCR_MG) {
-    set_error("wcl_invert_batch: the multigrid solver runs through wcl_invert, one lattice at a time");
+  if (params->solver == WCL_FGCR_MG || params->solver == WCL_FGCR_MG_BATCHED) {
+    set_error("wcl_invert_batch: the multigrid solvers run through wcl_invert, one lattice at a time");
     return WCL_ERR_INVALID_ARG;
   }
   std::vector<wcl_ctx*> v;

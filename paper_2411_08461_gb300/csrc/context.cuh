@@ -217,6 +217,8 @@ cudaError_t load_dslash_f64_module();
 // offset rhs_off_c of the caller's QDP buffers by FGCR preconditioned with the K-cycle
 void mg_free(wcl_ctx* c);
 void stag_free(wcl_ctx* c);
+// the batched K-cycle as a preconditioner of flexible GCR on M_hat (mg.cu): z_e = [K(r_e (+) 0)]_e
+wcl_status mg_batched_cycle(wcl_ctx* c, int nrhs, const void* r_even, void* z_even);
 wcl_status mg_solve_one(wcl_ctx* c, const void* d_b, void* d_x, long rhs_off_c, const wcl_solve_params& prm,
                         wcl_solve_info* info);
 

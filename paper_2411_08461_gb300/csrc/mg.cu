@@ -209,16 +209,24 @@ __global__ void __launch_bounds__(256) mg_orthonormalize_kernel(float2* __restri
   }
 }
 
-// c = P^+ v: one CTA per coarse site; the block's fine values are staged in shared memory
+// c = P^+ v: one CTA per (coarse site, right-hand side blockIdx.y); the block's fine
+// values are staged in shared memory.  pstride: float4 elements between the two parities
+// of one right-hand side (6 stride for one whole-lattice field, nrhs 6 stride for the
+// batched layout); rfine / rcoarse: offsets between right-hand sides.
 __global__ void __launch_bounds__(128) mg_restrict_kernel(const float4* __restrict__ v, const float2* __restrict__ P,
-                                                         MgGeom g, float2* __restrict__ out) {
+                                                         MgGeom g, float2* __restrict__ out, long pstride,
+                                                         long rfine, long rcoarse) {
   extern __shared__ float2 vs[];  // [bsites][12]
   const long c = blockIdx.x;
+  v += blockIdx.y * rfine;
+  out += blockIdx.y * rcoarse;
   for (int q = threadIdx.x; q < g.bsites * 12; q += blockDim.x) {
     int x[4];
     mg_site(g, c, q / 12, x);
     const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
-    vs[q] = fine_get(v, g.stride, p, mg_cb(g, x[0], x[1], x[2], x[3]), q % 12);
+    const int m = q % 12;
+    const float4 f = v[p * pstride + (long)(m / 2) * g.stride + mg_cb(g, x[0], x[1], x[2], x[3])];
+    vs[q] = (m & 1) ? make_float2(f.z, f.w) : make_float2(f.x, f.y);
   }
   __syncthreads();
   for (int j = threadIdx.x; j < g.n; j += blockDim.x) {
@@ -240,10 +248,13 @@ __global__ void __launch_bounds__(128) mg_restrict_kernel(const float4* __restri
   }
 }
 
-// v = P c (accumulate: v += P c): one thread per fine site
+// v = P c (accumulate: v += P c): one thread per fine site, right-hand side blockIdx.y
+// (pstride, rfine, rcoarse as for mg_restrict_kernel)
 __global__ void mg_prolong_kernel(const float2* __restrict__ cvec, const float2* __restrict__ P, MgGeom g,
-                                  float4* __restrict__ v, int accumulate) {
+                                  float4* __restrict__ v, int accumulate, long pstride, long rfine, long rcoarse) {
   const long vh = g.stride;  // padded sites per parity; padding rows of P are zero
+  cvec += blockIdx.y * rcoarse;
+  v += blockIdx.y * rfine;
   for (long site = blockIdx.x * (long)blockDim.x + threadIdx.x; site < 2 * vh;
        site += (long)gridDim.x * blockDim.x) {
     const int p = (int)(site / vh);
@@ -273,7 +284,7 @@ __global__ void mg_prolong_kernel(const float2* __restrict__ cvec, const float2*
     }
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-      float4* dst = v + ((long)p * 6 + q) * vh + i;
+      float4* dst = v + p * pstride + (long)q * vh + i;
       float4 val = make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
       if (accumulate) {
         const float4 old = *dst;
@@ -479,6 +490,261 @@ __global__ void __launch_bounds__(MG_MAX_N) mg_coarse_apply_kernel(const float2*
 }
 
 // ---------------------------------------------------------------------------
+// Batched K-cycle: nrhs right-hand sides at once, every coefficient on the device.
+// Batched fine fields: [parity][rhs][6][stride] float4 (the even half of all right-hand
+// sides is the library's nrhs parity field); batched coarse vectors [rhs][nc][n].
+
+// out_r = A_c in_r for MGB_RB right-hand sides per pass: the stencil block of a coarse
+// site is read once per pass instead of once per right-hand side
+constexpr int MGB_RB = 6;
+__global__ void __launch_bounds__(MG_MAX_N) mgb_coarse_apply_kernel(const float2* __restrict__ Y,
+                                                                   const float2* __restrict__ in, MgGeom g,
+                                                                   float2* __restrict__ out, int nrhs) {
+  __shared__ float2 vin[9][MGB_RB][MG_MAX_N];
+  const long c = blockIdx.x;
+  const int n = g.n;
+  const long rs = g.nc * n;
+  int cc[4];
+  long q = c;
+  for (int d = 0; d < 4; d++) {
+    cc[d] = (int)(q % g.cdims[d]);
+    q /= g.cdims[d];
+  }
+  long cn[9];
+  for (int k = 0; k < 9; k++) {
+    int dd[4] = {cc[0], cc[1], cc[2], cc[3]};
+    if (k > 0) {
+      const int mu = (k - 1) / 2;
+      const bool back = ((k - 1) & 1) != 0;
+      dd[mu] = back ? (dd[mu] == 0 ? g.cdims[mu] - 1 : dd[mu] - 1) : (dd[mu] + 1 == g.cdims[mu] ? 0 : dd[mu] + 1);
+    }
+    long v = 0;
+    for (int d = 3; d >= 0; d--) v = v * g.cdims[d] + dd[d];
+    cn[k] = v;
+  }
+  for (int r0 = 0; r0 < nrhs; r0 += MGB_RB) {
+    const int nr = min(MGB_RB, nrhs - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 9 * MGB_RB * n; e += blockDim.x) {
+      const int k = e / (MGB_RB * n), rr = (e / n) % MGB_RB, b = e % n;
+      vin[k][rr][b] = rr < nr ? in[(r0 + rr) * rs + cn[k] * n + b] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int ra = threadIdx.x;
+    if (ra < n) {
+      float re[MGB_RB], im[MGB_RB];
+#pragma unroll
+      for (int rr = 0; rr < MGB_RB; rr++) re[rr] = im[rr] = 0.f;
+      for (int k = 0; k < 9; k++) {
+        const float2* blk = Y + ((long)k * g.nc + c) * n * n;
+        for (int b = 0; b < n; b++) {
+          const float2 y = blk[b * n + ra];
+#pragma unroll
+          for (int rr = 0; rr < MGB_RB; rr++) {
+            const float2 v = vin[k][rr][b];
+            re[rr] = fmaf(y.x, v.x, fmaf(-y.y, v.y, re[rr]));
+            im[rr] = fmaf(y.x, v.y, fmaf(y.y, v.x, im[rr]));
+          }
+        }
+      }
+      for (int rr = 0; rr < nr; rr++) out[(r0 + rr) * rs + c * n + ra] = make_float2(re[rr], im[rr]);
+    }
+  }
+}
+
+// c_r = P^+ v_r for the batched layout: one CTA per (coarse site, right-hand side) with
+// the right-hand side fastest, so that the CTAs sharing a coarse site's rows of P run
+// together and read them from L2; the block's site offsets are computed once, and the
+// sums are FP32 (a preconditioner step; 6 bsites terms per output)
+__global__ void __launch_bounds__(128) mgb_restrict_kernel(const float4* __restrict__ v, const float2* __restrict__ P,
+                                                          MgGeom g, float2* __restrict__ out, int nrhs) {
+  extern __shared__ float2 vs[];  // [bsites][12], then the sites' P row bases
+  long* base = reinterpret_cast<long*>(vs + g.bsites * 12);
+  const long c = blockIdx.x / nrhs;
+  const int r = (int)(blockIdx.x % nrhs);
+  const long half = 6 * g.stride;
+  for (int s = threadIdx.x; s < g.bsites; s += blockDim.x) {
+    int x[4];
+    mg_site(g, c, s, x);
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const long i = mg_cb(g, x[0], x[1], x[2], x[3]);
+    base[s] = ((long)p * g.stride + i) * 12;
+    const float4* src = v + ((long)p * nrhs + r) * half + i;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      const float4 f = src[q * g.stride];
+      vs[s * 12 + 2 * q] = make_float2(f.x, f.y);
+      vs[s * 12 + 2 * q + 1] = make_float2(f.z, f.w);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < g.n; j += blockDim.x) {
+    const int chi = j / g.nv, k = j % g.nv;
+    float re = 0.f, im = 0.f;
+    for (int s = 0; s < g.bsites; s++) {
+      const long b0 = base[s] + chi * 6;
+#pragma unroll
+      for (int d = 0; d < 6; d++) {
+        const float2 u = P[(b0 + d) * g.nv + k], w = vs[s * 12 + chi * 6 + d];
+        re = fmaf(u.x, w.x, fmaf(u.y, w.y, re));
+        im = fmaf(u.x, w.y, fmaf(-u.y, w.x, im));
+      }
+    }
+    out[((long)r * g.nc + c) * g.n + j] = make_float2(re, im);
+  }
+}
+
+// v_r += P c_r for the batched layout: one thread per fine site applies each row of P,
+// read once, to every right-hand side (FP32 sums of nv terms)
+constexpr int MGB_MAXR = 12;
+__global__ void __launch_bounds__(128) mgb_prolong_kernel(const float2* __restrict__ cvec, const float2* __restrict__ P,
+                                                         MgGeom g, float4* __restrict__ v, int nrhs) {
+  const long vh = g.stride;
+  const long half = 6 * vh;
+  const long rs = g.nc * g.n;
+  for (long site = blockIdx.x * (long)blockDim.x + threadIdx.x; site < 2 * vh;
+       site += (long)gridDim.x * blockDim.x) {
+    const int p = (int)(site / vh);
+    const long i = site % vh;
+    const int xh = (int)(i % g.lxh);
+    long rem = i / g.lxh;
+    const int y = (int)(rem % g.dims[1]);
+    rem /= g.dims[1];
+    const int z = (int)(rem % g.dims[2]);
+    const int t = (int)(rem / g.dims[2]);
+    if (t >= g.dims[3]) continue;  // padding
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int xyzt[4] = {x, y, z, t};
+    const long c = mg_coarse_of(g, xyzt);
+    for (int q = 0; q < 6; q++) {
+      const int chi = (2 * q) / 6;
+      float2 a0[MGB_MAXR], a1[MGB_MAXR];
+#pragma unroll
+      for (int r = 0; r < MGB_MAXR; r++) a0[r] = a1[r] = make_float2(0.f, 0.f);
+      const float2* p0 = P + (site * 12 + 2 * q) * g.nv;
+      const float2* p1 = p0 + g.nv;
+      const float2* cv = cvec + c * g.n + chi * g.nv;
+      for (int k = 0; k < g.nv; k++) {
+        const float2 u0 = p0[k], u1 = p1[k];
+#pragma unroll
+        for (int r = 0; r < MGB_MAXR; r++) {
+          if (r >= nrhs) break;
+          const float2 w = cv[r * rs + k];
+          a0[r].x = fmaf(u0.x, w.x, fmaf(-u0.y, w.y, a0[r].x));
+          a0[r].y = fmaf(u0.x, w.y, fmaf(u0.y, w.x, a0[r].y));
+          a1[r].x = fmaf(u1.x, w.x, fmaf(-u1.y, w.y, a1[r].x));
+          a1[r].y = fmaf(u1.x, w.y, fmaf(u1.y, w.x, a1[r].y));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < MGB_MAXR; r++) {
+        if (r >= nrhs) break;
+        float4* dst = v + ((long)p * nrhs + r) * half + (long)q * vh + i;
+        const float4 old = *dst;
+        *dst = make_float4(old.x + a0[r].x, old.y + a0[r].y, old.z + a1[r].x, old.w + a1[r].y);
+      }
+    }
+  }
+}
+
+// The vector of right-hand side r is n complex numbers at r rstride and, with seg2 > 0,
+// n more at seg2 + r rstride (the odd half of a batched fine field).
+__device__ __forceinline__ long mgb_index(long k, long n, long off, long seg2) {
+  return k < n ? off + k : seg2 + off + (k - n);
+}
+
+// per right-hand side r = blockIdx.y: partial sums of <a_r, b_r> and, with c, <a_r, c_r>
+// (conj(a) b); part[((r * gridDim.x) + block) * 4 + {0..3}]
+__global__ void __launch_bounds__(256) mgb_dot_kernel(const float2* __restrict__ a, const float2* __restrict__ b,
+                                                      const float2* __restrict__ c, long n, long rstride, long seg2,
+                                                      double* __restrict__ part) {
+  const long off = blockIdx.y * rstride;
+  const long ntot = seg2 > 0 ? 2 * n : n;
+  double v[4] = {0, 0, 0, 0};
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < ntot; k += (long)gridDim.x * blockDim.x) {
+    const long q = mgb_index(k, n, off, seg2);
+    const float2 x = a[q], y = b[q];
+    v[0] += (double)x.x * y.x + (double)x.y * y.y;
+    v[1] += (double)x.x * y.y - (double)x.y * y.x;
+    if (c) {
+      const float2 z = c[q];
+      v[2] += (double)x.x * z.x + (double)x.y * z.y;
+      v[3] += (double)x.x * z.y - (double)x.y * z.x;
+    }
+  }
+  __shared__ double sh[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const double t = warp_sum(v[j]);
+    if (lane == 0) sh[j][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[threadIdx.x][k];
+    part[((long)blockIdx.y * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = t;
+  }
+}
+
+// coefficients from the summed dots of right-hand side r = threadIdx.x (fixed order):
+//   MGB_MR       alpha = <a,c> / <a,a>: ca = alpha, cb = -alpha    (minimal residual: a = M r, c = r)
+//   MGB_PROJ     beta = <a,b>:          ca = -beta                  (Gram-Schmidt)
+//   MGB_NORMINV  ca = 1 / sqrt(<a,a>)  (0 for a zero vector)
+//   MGB_COEF     al = <a,b>:            ca = al, cb = -al
+enum { MGB_MR = 0, MGB_PROJ = 1, MGB_NORMINV = 2, MGB_COEF = 3 };
+__global__ void mgb_coef_kernel(const double* __restrict__ part, int nblk, int nrhs, int mode, float2* __restrict__ ca,
+                                float2* __restrict__ cb) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  double s[4] = {0, 0, 0, 0};
+  for (int k = 0; k < nblk; k++)
+    for (int j = 0; j < 4; j++) s[j] += part[((long)r * nblk + k) * 4 + j];
+  float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+  if (mode == MGB_MR) {
+    if (s[0] > 0) {
+      a = make_float2((float)(s[2] / s[0]), (float)(s[3] / s[0]));
+      b = make_float2(-a.x, -a.y);
+    }
+  } else if (mode == MGB_PROJ) {
+    a = make_float2((float)-s[0], (float)-s[1]);
+  } else if (mode == MGB_NORMINV) {
+    if (s[0] > 0) a = make_float2((float)(1.0 / sqrt(s[0])), 0.f);
+  } else {
+    a = make_float2((float)s[0], (float)s[1]);
+    b = make_float2(-a.x, -a.y);
+  }
+  ca[r] = a;
+  if (cb) cb[r] = b;
+}
+
+// y_r += coef[r] x_r (x given) or y_r = coef[r] y_r (x null), r = blockIdx.y
+__global__ void mgb_axpy_kernel(float2* __restrict__ y, const float2* __restrict__ x, const float2* __restrict__ coef,
+                                long n, long rstride, long seg2) {
+  const long off = blockIdx.y * rstride;
+  const long ntot = seg2 > 0 ? 2 * n : n;
+  const float2 a = coef[blockIdx.y];
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < ntot; k += (long)gridDim.x * blockDim.x) {
+    const long q = mgb_index(k, n, off, seg2);
+    const float2 v = y[q];
+    if (x) {
+      const float2 u = x[q];
+      y[q] = make_float2(v.x + a.x * u.x - a.y * u.y, v.y + a.x * u.y + a.y * u.x);
+    } else {
+      y[q] = make_float2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
+    }
+  }
+}
+
+// y = x - y elementwise (float2), the whole batch
+__global__ void mgb_rsub_kernel(float2* __restrict__ y, const float2* __restrict__ x, long n) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const float2 u = x[k], v = y[k];
+    y[k] = make_float2(u.x - v.x, u.y - v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 full-field helpers for the defect correction (even then odd parity, F64 layout)
 __global__ void mg_sub64_kernel(double2* __restrict__ r, const double2* __restrict__ b, const double2* __restrict__ y,
                                 long n) {  // r = b - y
@@ -607,13 +873,14 @@ struct Ctx {
   }
   wcl_status restrict_(float2* out, const float4* in) {
     const size_t sm = sizeof(float2) * m->g.bsites * 12;
-    mg_restrict_kernel<<<(unsigned)m->g.nc, 128, sm, c->stream>>>(in, m->P, m->g, out);
+    mg_restrict_kernel<<<(unsigned)m->g.nc, 128, sm, c->stream>>>(in, m->P, m->g, out, 6 * m->g.stride, 0, 0);
     WCL_CUDA(cudaGetLastError());
     count_launch(c);
     return WCL_OK;
   }
   wcl_status prolong(float4* out, const float2* in, bool accumulate) {
-    mg_prolong_kernel<<<grid_of(2 * m->g.stride), 256, 0, c->stream>>>(in, m->P, m->g, out, accumulate ? 1 : 0);
+    mg_prolong_kernel<<<grid_of(2 * m->g.stride), 256, 0, c->stream>>>(in, m->P, m->g, out, accumulate ? 1 : 0,
+                                                                      6 * m->g.stride, 0, 0);
     WCL_CUDA(cudaGetLastError());
     count_launch(c);
     return WCL_OK;
@@ -715,6 +982,167 @@ struct Ctx {
   }
 };
 
+// The K-cycle on nr right-hand sides at once (batched layouts above): the same steps as
+// Ctx::cycle, with the minimal-residual and Gram-Schmidt coefficients of every
+// right-hand side computed and consumed on the device, and a fixed number of coarse GCR
+// steps (coarse_maxiter; restarted every coarse_nkrylov), so nothing waits on the host.
+struct BCtx {
+  wcl_ctx* c;
+  MgState* m;
+  int nr;
+  float4* in;   // the right-hand sides of the cycle
+  float4* e;    // its result
+  float4* rr;   // minimal-residual residual
+  float4* ar;   // M rr
+  float4* t;    // M e, then the fine residual restricted
+  float2* cw;   // coarse: b, r, x, Z[nk], W[nk]
+  double* part;
+  float2* ca;
+  float2* cb;
+  int gb = 1;
+
+  long half() const { return 6 * m->g.stride; }            // float4 in one parity of one RHS
+  long pc() const { return 12 * m->g.stride; }              // complex numbers in one parity of one RHS
+  long fine_c() const { return 2 * nr * pc(); }             // complex numbers of a whole batched field
+  long ncv() const { return m->g.nc * m->g.n; }             // complex numbers of one coarse vector
+  int nk() const { return std::max(1, std::min(m->prm.coarse_nkrylov, 64)); }
+  float2* cvec(int k) const { return cw + (size_t)k * nr * ncv(); }
+
+  wcl_status alloc(int nrhs) {
+    nr = nrhs;
+    const size_t fb = sizeof(float4) * 2 * nr * half();
+    void* q;
+    WCL_CHECK(ws_get(c, "mgb_fine", fb * 5, &q));
+    in = static_cast<float4*>(q);
+    e = in + 2 * nr * half();
+    rr = e + 2 * nr * half();
+    ar = rr + 2 * nr * half();
+    t = ar + 2 * nr * half();
+    WCL_CHECK(ws_get(c, "mgb_coarse", sizeof(float2) * nr * ncv() * (3 + 2 * nk()), &q));
+    cw = static_cast<float2*>(q);
+    gb = std::min(256, grid_of(2 * pc()));
+    WCL_CHECK(ws_get(c, "mgb_part", sizeof(double) * 4 * nr * std::max(gb, 256), &q));
+    part = static_cast<double*>(q);
+    WCL_CHECK(ws_get(c, "mgb_coef", sizeof(float2) * 2 * nr, &q));
+    ca = static_cast<float2*>(q);
+    cb = ca + nr;
+    return WCL_OK;
+  }
+  wcl_status apply_M(float4* out, const float4* x) {
+    std::vector<wcl_ctx*> v{c};
+    FieldRef ie{}, io{}, oe{}, oo{};
+    ie.ptr[0] = const_cast<float4*>(x);
+    io.ptr[0] = const_cast<float4*>(x) + nr * half();
+    oe.ptr[0] = out;
+    oo.ptr[0] = out + nr * half();
+    WCL_CHECK(dslash(v, F32, nr, oe, io, &ie, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
+    WCL_CHECK(dslash(v, F32, nr, oo, ie, &io, 1, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, nullptr));
+    return WCL_OK;
+  }
+  // coefficients of every right-hand side from <a, b> (and <a, cc>); fine: batched fine
+  // fields (both parities), else coarse vectors
+  wcl_status coef(const float2* a, const float2* b, const float2* cc, bool fine, int mode) {
+    const long n = fine ? pc() : ncv();
+    const long rs = fine ? pc() : ncv();
+    const long seg2 = fine ? nr * pc() : 0;
+    const int g = fine ? gb : std::min(64, grid_of(n));
+    mgb_dot_kernel<<<dim3(g, nr), 256, 0, c->stream>>>(a, b, cc, n, rs, seg2, part);
+    WCL_CUDA(cudaGetLastError());
+    mgb_coef_kernel<<<1, 32 * ((nr + 31) / 32), 0, c->stream>>>(part, g, nr, mode, ca, cb);
+    WCL_CUDA(cudaGetLastError());
+    count_launch(c);
+    count_launch(c);
+    return WCL_OK;
+  }
+  wcl_status axpy(float2* y, const float2* x, const float2* k, bool fine) {
+    const long n = fine ? pc() : ncv();
+    const long rs = n;
+    const long seg2 = fine ? nr * pc() : 0;
+    mgb_axpy_kernel<<<dim3(std::min(grid_of(fine ? 2 * n : n), 152 * 4), nr), 256, 0, c->stream>>>(y, x, k, n, rs, seg2);
+    WCL_CUDA(cudaGetLastError());
+    count_launch(c);
+    return WCL_OK;
+  }
+  // `steps` minimal-residual steps on M x = b from x (x0: r = b - M x; else x = 0, r = b)
+  wcl_status minres(float4* x, const float4* b, int steps, bool x0) {
+    const long n = fine_c();
+    if (x0) {
+      // rr = b - M x (mgb_rsub_kernel forms y = x - y in place)
+      WCL_CHECK(apply_M(ar, x));
+      WCL_CUDA(cudaMemcpyAsync(rr, ar, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream));
+      mgb_rsub_kernel<<<grid_of(n), 256, 0, c->stream>>>((float2*)rr, (const float2*)b, n);
+      WCL_CUDA(cudaGetLastError());
+      count_launch(c);
+    } else {
+      WCL_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * n, c->stream));
+      WCL_CUDA(cudaMemcpyAsync(rr, b, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    for (int s = 0; s < steps; s++) {
+      WCL_CHECK(apply_M(ar, rr));
+      WCL_CHECK(coef((const float2*)ar, (const float2*)ar, (const float2*)rr, true, MGB_MR));
+      WCL_CHECK(axpy((float2*)x, (const float2*)rr, ca, true));
+      WCL_CHECK(axpy((float2*)rr, (const float2*)ar, cb, true));
+    }
+    return WCL_OK;
+  }
+  // coarse GCR on A_c x = b from x = 0, a fixed number of steps
+  wcl_status coarse_solve(float2* x, const float2* b, int steps) {
+    const long n = (long)nr * ncv();
+    float2* r = cvec(1);
+    float2* Z = cvec(3);
+    float2* W = cvec(3 + nk());
+    WCL_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * n, c->stream));
+    WCL_CUDA(cudaMemcpyAsync(r, b, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream));
+    int k = 0;
+    for (int it = 0; it < steps; it++) {
+      if (k == nk()) k = 0;
+      float2* z = Z + (size_t)k * nr * ncv();
+      float2* w = W + (size_t)k * nr * ncv();
+      WCL_CUDA(cudaMemcpyAsync(z, r, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream));
+      mgb_coarse_apply_kernel<<<(unsigned)m->g.nc, MG_MAX_N, 0, c->stream>>>(m->Y, z, m->g, w, nr);
+      WCL_CUDA(cudaGetLastError());
+      count_launch(c);
+      for (int j = 0; j < k; j++) {
+        const float2* wj = W + (size_t)j * nr * ncv();
+        const float2* zj = Z + (size_t)j * nr * ncv();
+        WCL_CHECK(coef(wj, w, nullptr, false, MGB_PROJ));
+        WCL_CHECK(axpy(w, wj, ca, false));
+        WCL_CHECK(axpy(z, zj, ca, false));
+      }
+      WCL_CHECK(coef(w, w, nullptr, false, MGB_NORMINV));
+      WCL_CHECK(axpy(w, nullptr, ca, false));
+      WCL_CHECK(axpy(z, nullptr, ca, false));
+      WCL_CHECK(coef(w, r, nullptr, false, MGB_COEF));
+      WCL_CHECK(axpy(x, z, ca, false));
+      WCL_CHECK(axpy(r, w, cb, false));
+      k++;
+    }
+    return WCL_OK;
+  }
+  // e = K-cycle(in)
+  wcl_status cycle() {
+    const MgGeom& g = m->g;
+    WCL_CHECK(minres(e, in, m->prm.pre, false));
+    WCL_CHECK(apply_M(t, e));
+    mgb_rsub_kernel<<<grid_of(fine_c()), 256, 0, c->stream>>>((float2*)t, (const float2*)in, fine_c());
+    WCL_CUDA(cudaGetLastError());
+    count_launch(c);
+    float2* rc = cvec(0);
+    float2* ec = cvec(2);
+    const size_t sm = sizeof(float2) * g.bsites * 12 + sizeof(long) * g.bsites;
+    mgb_restrict_kernel<<<(unsigned)(g.nc * nr), 128, sm, c->stream>>>(t, m->P, g, rc, nr);
+    WCL_CUDA(cudaGetLastError());
+    count_launch(c);
+    WCL_CHECK(coarse_solve(ec, rc, std::max(1, m->prm.coarse_maxiter)));
+    mgb_prolong_kernel<<<(unsigned)std::min((2 * g.stride + 127) / 128, 152L * 16), 128, 0, c->stream>>>(ec, m->P, g, e,
+                                                                                                     nr);
+    WCL_CUDA(cudaGetLastError());
+    count_launch(c);
+    if (m->prm.post > 0) WCL_CHECK(minres(e, in, m->prm.post, true));
+    return WCL_OK;
+  }
+};
+
 // import a QDP complex128 full field (device or page-locked host) into a fine FP32 field
 wcl_status import_full32(wcl_ctx* c, const void* src, float4* dst, long rhs_off_c) {
   std::vector<wcl_ctx*> v{c};
@@ -767,6 +1195,22 @@ wcl_status check_ready(wcl_ctx* c, const char* what) {
 }
 
 }  // namespace
+
+// z_e = [K(r_e (+) 0)]_e for nrhs even-site FP32 fields (the library's nrhs parity-field
+// layout, consecutive right-hand sides): the batched K-cycle of the whole-lattice M
+// applied to the residual embedded with zero odd sites.  Since the even-even block of
+// M^-1 is M_hat^-1, this preconditions flexible GCR on M_hat (WCL_FGCR_MG_BATCHED).
+wcl_status mg_batched_cycle(wcl_ctx* c, int nrhs, const void* r_even, void* z_even) {
+  WCL_CHECK(check_ready(c, "batched multigrid cycle"));
+  BCtx b{c, mg_of(c)};
+  WCL_CHECK(b.alloc(nrhs));
+  const size_t pb = sizeof(float4) * nrhs * b.half();
+  WCL_CUDA(cudaMemcpyAsync(b.in, r_even, pb, cudaMemcpyDeviceToDevice, c->stream));
+  WCL_CUDA(cudaMemsetAsync(b.in + nrhs * b.half(), 0, pb, c->stream));
+  WCL_CHECK(b.cycle());
+  WCL_CUDA(cudaMemcpyAsync(z_even, b.e, pb, cudaMemcpyDeviceToDevice, c->stream));
+  return WCL_OK;
+}
 
 // the flexible-GCR solve of M x = b, one right-hand side, preconditioned by the K-cycle,
 // in FP32 between FP64 true-residual restarts (used by wcl_invert with WCL_FGCR_MG)
@@ -1060,6 +1504,40 @@ wcl_status wcl_mg_cycle(wcl_ctx* c, void* d_out, const void* d_in, int* coarse_i
   if (s == WCL_OK) s = export_full32(c, k.fine(4), out);
   if (coarse_iters) *coarse_iters = ci;
   return wcl_leave(c, s);
+}
+
+wcl_status wcl_mg_cycle_batched(wcl_ctx* c, void* d_out, const void* d_in, int nrhs) {
+  if (!c || !d_out || !d_in || nrhs < 1 || nrhs > 12) {
+    set_error("wcl_mg_cycle_batched: invalid argument (1 <= nrhs <= 12)");
+    return WCL_ERR_INVALID_ARG;
+  }
+  WCL_CHECK(check_ready(c, "wcl_mg_cycle_batched"));
+  const void* in = nullptr;
+  const void* outc = nullptr;
+  if (!wcl_resolve_field(c, d_in, &in, "wcl_mg_cycle_batched in") ||
+      !wcl_resolve_field(c, d_out, &outc, "wcl_mg_cycle_batched out"))
+    return WCL_ERR_INVALID_ARG;
+  WCL_CHECK(wcl_enter(c));
+  BCtx b{c, mg_of(c)};
+  WCL_CHECK(b.alloc(nrhs));
+  Ctx k{c, mg_of(c)};
+  float4* tmp = k.fine(0);  // one whole-lattice FP32 field: [even 6 x stride][odd 6 x stride]
+  const long h = b.half();
+  const long rs = 2 * c->lat.vh * 12;
+  for (int r = 0; r < nrhs; r++) {
+    WCL_CHECK(import_full32(c, static_cast<const double2*>(in) + (long)r * rs, tmp, 0));
+    WCL_CUDA(cudaMemcpyAsync(b.in + r * h, tmp, sizeof(float4) * h, cudaMemcpyDeviceToDevice, c->stream));
+    WCL_CUDA(cudaMemcpyAsync(b.in + (nrhs + r) * h, tmp + h, sizeof(float4) * h, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  }
+  WCL_CHECK(b.cycle());
+  for (int r = 0; r < nrhs; r++) {
+    WCL_CUDA(cudaMemcpyAsync(tmp, b.e + r * h, sizeof(float4) * h, cudaMemcpyDeviceToDevice, c->stream));
+    WCL_CUDA(cudaMemcpyAsync(tmp + h, b.e + (nrhs + r) * h, sizeof(float4) * h, cudaMemcpyDeviceToDevice,
+                             c->stream));
+    WCL_CHECK(export_full32(c, tmp, static_cast<double2*>(const_cast<void*>(outc)) + (long)r * rs));
+  }
+  return wcl_leave(c, WCL_OK);
 }
 
 wcl_status wcl_mg_restrict(wcl_ctx* c, void* d_coarse, const void* d_fine) {

@@ -318,7 +318,7 @@ struct KrylovSolver {
   // (as stable as modified Gram-Schmidt, two passes instead of k), then
   // alpha = <w_k, r>/||w_k||^2, x += alpha z_k, r -= alpha w_k, and w_k, z_k
   // rescaled to unit ||w_k||.  Every restart is a reliable update.
-  wcl_status loop_gcr(int& nactive, bool learned) {
+  wcl_status loop_gcr(int& nactive, bool learned, bool mgb = false) {
     const int m = std::min(std::max(1, prm.gcr_nkrylov), GCR_MAXK);
     FieldRef Z{}, W{}, r32{}, z32{};
     long vstride[MAXLAT] = {}, nvstride[MAXLAT] = {};
@@ -358,7 +358,9 @@ struct KrylovSolver {
     int k = 0;
     while (nactive > 0) {
       const FieldRef Zk = vec(Z, k), Wk = vec(W, k);
-      if (learned) {
+      if (mgb) {
+        WCL_CHECK(mg_batched_cycle(c0, nrhs, r.ptr[0], Zk.ptr[0]));
+      } else if (learned) {
         if (S == F32) {
           WCL_CHECK(ptc_apply(ctxs, nrhs, r, Zk, 1));
         } else {
@@ -451,7 +453,7 @@ struct KrylovSolver {
     auto t0 = std::chrono::steady_clock::now();
     c0 = ctxs[0];
     nslot = (int)ctxs.size() * nrhs;
-    gcr = prm.solver == WCL_FGCR_LEARNED || prm.solver == WCL_GCR;
+    gcr = prm.solver == WCL_FGCR_LEARNED || prm.solver == WCL_GCR || prm.solver == WCL_FGCR_MG_BATCHED;
     cg = prm.solver == WCL_CGNR || gcr;  // GCR residual replacement keeps no BiCGStab state
     blk = c0->blas_block;
     bb = make_batch(ctxs, nrhs, blk, RED_MAXCH);
@@ -531,7 +533,7 @@ struct KrylovSolver {
 
     const int ce = std::max(1, prm.check_every);
     const double d2 = prm.delta_reliable * prm.delta_reliable;
-    if (gcr) WCL_CHECK(loop_gcr(nactive, prm.solver == WCL_FGCR_LEARNED));
+    if (gcr) WCL_CHECK(loop_gcr(nactive, prm.solver == WCL_FGCR_LEARNED, prm.solver == WCL_FGCR_MG_BATCHED));
     // events inside captured graphs cannot be timed: profiling launches directly
     bool graphs = prm.use_graphs != 0 && !c0->profiling;
     if (graphs && !gcr) {

@@ -21,7 +21,7 @@ STATUS_NAMES = {
     9: "WCL_ERR_NO_GAUGE", 10: "WCL_ERR_NO_PRECOND",
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
-SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3, "fgcr_mg": 4}
+SOLVER = {"bicgstab": 0, "cgnr": 1, "fgcr_learned": 2, "gcr": 3, "fgcr_mg": 4, "fgcr_mg_batched": 5}
 PTC_NWEIGHTS = 5760
 WCL_OPT_TENSOR_CORES = 1
 WCL_OPT_SHARED_LINKS = 2
@@ -128,6 +128,7 @@ SIGNATURES = {
     "wcl_default_mg_params": (None, [ctypes.POINTER(wcl_mg_params)]),
     "wcl_mg_setup": (ctypes.c_int, [_P, _P, ctypes.POINTER(wcl_mg_params)]),
     "wcl_mg_cycle": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "wcl_mg_cycle_batched": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "wcl_mg_restrict": (ctypes.c_int, [_P, _P, _P]),
     "wcl_mg_prolong": (ctypes.c_int, [_P, _P, _P]),
     "wcl_mg_coarse_apply": (ctypes.c_int, [_P, _P, _P]),
@@ -374,6 +375,14 @@ class Context:
                                            _ptr(inp, torch.complex128, self.fermion_numel, "in", True),
                                            ctypes.byref(it)), "wcl_mg_cycle")
         return it.value
+
+    def wcl_mg_cycle_batched(self, out, inp, nrhs: int):
+        import torch
+
+        n = self.fermion_numel * nrhs
+        _check(load_library().wcl_mg_cycle_batched(self.handle, _ptr(out, torch.complex128, n, "out", True),
+                                                   _ptr(inp, torch.complex128, n, "in", True), int(nrhs)),
+               "wcl_mg_cycle_batched")
 
     def wcl_mg_restrict(self, coarse, fine):
         import torch

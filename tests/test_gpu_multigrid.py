@@ -149,6 +149,56 @@ def test_k_cycle_matches_oracle(pkg, pre, post):
     ctx.close()
 
 
+@pytest.mark.parametrize("nrhs", [1, 7])
+def test_batched_k_cycle_matches_oracle(pkg, nrhs):
+    """The batched K-cycle (coefficients per right-hand side on the device, the coarse
+    stencil read once for up to six right-hand sides: 7 is one full and one ragged pass)
+    equals the oracle's cycle on the library's P for every right-hand side, with a fixed
+    number of coarse steps that spans a restart of the coarse GCR."""
+    dims, block, nv = (4, 4, 4, 8), (2, 2, 2, 2), 4
+    kw = dict(pre=2, post=2, coarse_tol=0.0, coarse_maxiter=6, coarse_nkrylov=4)
+    ctx, op, starts = _setup(pkg, dims, block, nv, relax=3, kappa=0.124, **kw)
+    P = _oracle_P(dims, block, [L.from_qdp(s, dims) for s in starts], _gpu_basis(ctx, dims, block, nv))
+    lvl = MG.Level(op.M, P, None, **kw)
+    r = W.gaussian_fermion(dims, 90, nrhs=nrhs)
+    e = cuda(np.zeros_like(r))
+    ctx.wcl_mg_cycle_batched(e, cuda(r), nrhs)
+    eh = host(e)
+    for k in range(nrhs):
+        assert relerr(L.from_qdp(eh[k], dims), lvl.cycle(L.from_qdp(r[k], dims))) <= 1e-4, k
+    ctx.close()
+
+
+def test_batched_multigrid_fgcr_solve(pkg):
+    """All right-hand sides at once: flexible GCR on M_hat preconditioned by the batched
+    K-cycle reaches 1e-10 (true residual recomputed by the oracle) near the critical kappa,
+    in under half the iterations of GCR(20) on M_hat without the preconditioner (measured:
+    27 against 79; M_hat is better conditioned than the whole-lattice M of the test above,
+    so the gain is smaller than there)."""
+    dims = (8, 8, 8, 8)
+    kappa = 0.1255
+    gauge = W.gauge_links(dims, 0.3, 5)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), kappa, 1.0)
+    op = dirac.from_qdp_problem(gauge, dims, kappa, 1.0)
+    starts = W.gaussian_fermion(dims, 200, nrhs=8)
+    ctx.wcl_mg_setup(cuda(starts), pkg.wcl_default_mg_params(block=(2, 2, 2, 2), nvec=8, relax_steps=20,
+                                                             coarse_maxiter=8))
+    b = np.stack([W.point_source(dims, s, c) for s, c in [(0, 0), (1, 2), (3, 1)]] + [W.gaussian_fermion(dims, 201)])
+    x = cuda(np.zeros_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 4, pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=1e-10,
+                                                                   gcr_nkrylov=20))
+    xh = host(x)
+    for k in range(4):
+        tr = op.true_residual(L.from_qdp(xh[k], dims), L.from_qdp(b[k], dims))
+        assert tr <= 1e-10, (k, tr, info)
+        assert info[k]["status"] == 0
+    _, gcr = ctx.wcl_invert(cuda(np.zeros_like(b)), cuda(b), 4, pkg.wcl_default_params(solver="gcr", sloppy="f32",
+                                                                                        tol=1e-10, gcr_nkrylov=20))
+    assert info[0]["iters"] * 2 <= gcr[0]["iters"], (info[0]["iters"], gcr[0]["iters"])
+    ctx.close()
+
+
 def test_multigrid_fgcr_solve(pkg):
     """FGCR with the two-level K-cycle reaches the requested 1e-10 (true residual recomputed
     by the oracle) near the critical kappa in far fewer outer iterations than the oracle's
@@ -185,6 +235,13 @@ def test_multigrid_errors(pkg):
         ctx.wcl_invert(cuda(np.zeros((1,) + tuple(b.shape[1:]), dtype=np.complex128)), b, 1,
                        pkg.wcl_default_params(solver="fgcr_mg"))
     assert e.value.status == 10
+    with pytest.raises(WclError) as e:
+        ctx.wcl_invert(cuda(np.zeros((1,) + tuple(b.shape[1:]), dtype=np.complex128)), b, 1,
+                       pkg.wcl_default_params(solver="fgcr_mg_batched"))
+    assert e.value.status == 10
+    with pytest.raises(WclError) as e:
+        ctx.wcl_mg_cycle_batched(cuda(np.zeros((1,) + tuple(b.shape[1:]), dtype=np.complex128)), b, 1)
+    assert e.value.status == 10
     starts = cuda(W.gaussian_fermion(dims, 3, nrhs=2))
     with pytest.raises(WclError) as e:  # 3 does not divide 4
         ctx.wcl_mg_setup(starts, pkg.wcl_default_mg_params(block=(3, 2, 2, 2), nvec=2))
@@ -192,5 +249,10 @@ def test_multigrid_errors(pkg):
     with pytest.raises(WclError) as e:  # more vectors than block degrees of freedom (1 site x 6)
         ctx.wcl_mg_setup(cuda(W.gaussian_fermion(dims, 4, nrhs=7)),
                          pkg.wcl_default_mg_params(block=(1, 1, 1, 1), nvec=7))
+    assert e.value.status == 1
+    ctx.wcl_mg_setup(starts, pkg.wcl_default_mg_params(block=(2, 2, 2, 2), nvec=2))
+    with pytest.raises(WclError) as e:  # the batched multigrid runs an FP32 inner solver only
+        ctx.wcl_invert(cuda(np.zeros((1,) + tuple(b.shape[1:]), dtype=np.complex128)), b, 1,
+                       pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f16"))
     assert e.value.status == 1
     ctx.close()
