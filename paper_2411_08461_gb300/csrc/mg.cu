@@ -554,11 +554,15 @@ __global__ void __launch_bounds__(MG_MAX_N) mgb_coarse_apply_kernel(const float2
 
 // c_r = P^+ v_r for the batched layout: one CTA per (coarse site, right-hand side) with
 // the right-hand side fastest, so that the CTAs sharing a coarse site's rows of P run
-// together and read them from L2; the block's site offsets are computed once, and the
-// sums are FP32 (a preconditioner step; 6 bsites terms per output)
-__global__ void __launch_bounds__(128) mgb_restrict_kernel(const float4* __restrict__ v, const float2* __restrict__ P,
-                                                          MgGeom g, float2* __restrict__ out, int nrhs) {
+// together and read them from L2; the block's site offsets are computed once; the
+// MGB_RG groups of the CTA's threads each sum a quarter of the sites for every output
+// (FP32 sums: a preconditioner step), then the groups' sums are added
+constexpr int MGB_RG = 4;
+__global__ void __launch_bounds__(MGB_RG * MG_MAX_N) mgb_restrict_kernel(const float4* __restrict__ v,
+                                                                        const float2* __restrict__ P, MgGeom g,
+                                                                        float2* __restrict__ out, int nrhs) {
   extern __shared__ float2 vs[];  // [bsites][12], then the sites' P row bases
+  __shared__ float2 red[MGB_RG][MG_MAX_N];
   long* base = reinterpret_cast<long*>(vs + g.bsites * 12);
   const long c = blockIdx.x / nrhs;
   const int r = (int)(blockIdx.x % nrhs);
@@ -578,10 +582,11 @@ __global__ void __launch_bounds__(128) mgb_restrict_kernel(const float4* __restr
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < g.n; j += blockDim.x) {
+  const int j = threadIdx.x % MG_MAX_N, grp = threadIdx.x / MG_MAX_N;
+  if (j < g.n) {
     const int chi = j / g.nv, k = j % g.nv;
     float re = 0.f, im = 0.f;
-    for (int s = 0; s < g.bsites; s++) {
+    for (int s = grp; s < g.bsites; s += MGB_RG) {
       const long b0 = base[s] + chi * 6;
 #pragma unroll
       for (int d = 0; d < 6; d++) {
@@ -590,7 +595,13 @@ __global__ void __launch_bounds__(128) mgb_restrict_kernel(const float4* __restr
         im = fmaf(u.x, w.y, fmaf(-u.y, w.x, im));
       }
     }
-    out[((long)r * g.nc + c) * g.n + j] = make_float2(re, im);
+    red[grp][j] = make_float2(re, im);
+  }
+  __syncthreads();
+  if (grp == 0 && j < g.n) {
+    float2 t = red[0][j];
+    for (int q = 1; q < MGB_RG; q++) t = make_float2(t.x + red[q][j].x, t.y + red[q][j].y);
+    out[((long)r * g.nc + c) * g.n + j] = t;
   }
 }
 
@@ -654,24 +665,27 @@ __device__ __forceinline__ long mgb_index(long k, long n, long off, long seg2) {
 }
 
 // per right-hand side r = blockIdx.y: partial sums of <a_r, b_r> and, with c, <a_r, c_r>
-// (conj(a) b); part[((r * gridDim.x) + block) * 4 + {0..3}]
+// (conj(a) b); part[((r * gridDim.x) + block) * 4 + {0..3}].  Each thread sums its
+// elements in FP32 (GB300's FP64 rate made FP64 products the cost of this kernel), the
+// threads' sums are added in FP64.
 __global__ void __launch_bounds__(256) mgb_dot_kernel(const float2* __restrict__ a, const float2* __restrict__ b,
                                                       const float2* __restrict__ c, long n, long rstride, long seg2,
                                                       double* __restrict__ part) {
   const long off = blockIdx.y * rstride;
   const long ntot = seg2 > 0 ? 2 * n : n;
-  double v[4] = {0, 0, 0, 0};
+  float f[4] = {0.f, 0.f, 0.f, 0.f};
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < ntot; k += (long)gridDim.x * blockDim.x) {
     const long q = mgb_index(k, n, off, seg2);
     const float2 x = a[q], y = b[q];
-    v[0] += (double)x.x * y.x + (double)x.y * y.y;
-    v[1] += (double)x.x * y.y - (double)x.y * y.x;
+    f[0] = fmaf(x.x, y.x, fmaf(x.y, y.y, f[0]));
+    f[1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, f[1]));
     if (c) {
       const float2 z = c[q];
-      v[2] += (double)x.x * z.x + (double)x.y * z.y;
-      v[3] += (double)x.x * z.y - (double)x.y * z.x;
+      f[2] = fmaf(x.x, z.x, fmaf(x.y, z.y, f[2]));
+      f[3] = fmaf(x.x, z.y, fmaf(-x.y, z.x, f[3]));
     }
   }
+  double v[4] = {f[0], f[1], f[2], f[3]};
   __shared__ double sh[4][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -1130,7 +1144,7 @@ struct BCtx {
     float2* rc = cvec(0);
     float2* ec = cvec(2);
     const size_t sm = sizeof(float2) * g.bsites * 12 + sizeof(long) * g.bsites;
-    mgb_restrict_kernel<<<(unsigned)(g.nc * nr), 128, sm, c->stream>>>(t, m->P, g, rc, nr);
+    mgb_restrict_kernel<<<(unsigned)(g.nc * nr), MGB_RG * MG_MAX_N, sm, c->stream>>>(t, m->P, g, rc, nr);
     WCL_CUDA(cudaGetLastError());
     count_launch(c);
     WCL_CHECK(coarse_solve(ec, rc, std::max(1, m->prm.coarse_maxiter)));
