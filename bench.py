@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--kappa", type=float, default=KAPPA, help="hopping parameter of --case mg")
     ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
     ap.add_argument("--mg-nvec", type=int, default=24, help="--case mg: null vectors")
+    ap.add_argument("--mg-nkrylov", type=int, default=20, help="--case mg: restart length of the outer FGCR")
     ap.add_argument("--mg-coarse-steps", type=int, default=8,
                     help="--case mg: coarse GCR steps of the batched K-cycle (solver fgcr_mg_batched)")
     ap.add_argument("--mg-single", type=int, default=1,
@@ -1014,7 +1015,7 @@ def run_mg_case(args):
     line = {"case": "mg", "lattice": dims, "kappa": args.kappa, "block": block, "nvec": args.mg_nvec,
             "relax_steps": mprm.relax_steps, "setup_seconds": setup_s}
     if args.mg_single:
-        mg = pkg.wcl_default_params(solver="fgcr_mg", tol=args.tol, gcr_nkrylov=20)
+        mg = pkg.wcl_default_params(solver="fgcr_mg", tol=args.tol, gcr_nkrylov=args.mg_nkrylov)
         ctx.wcl_invert(x[:1], src[:1], 1, mg)  # warm-up
         mg_s, infos = timed(lambda: ctx.wcl_invert(x, src, 12, mg)[1])
         line["mg_fgcr"] = {"seconds": mg_s, "outer_iters_per_rhs": float(np.mean([i["iters"] for i in infos])),
@@ -1026,11 +1027,11 @@ def run_mg_case(args):
     bprm = pkg.wcl_default_mg_params(block=block, nvec=args.mg_nvec, coarse_maxiter=args.mg_coarse_steps)
     ctx.wcl_mg_setup(starts, bprm)
     del starts
-    mgb = pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=args.tol, gcr_nkrylov=20,
+    mgb = pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=args.tol, gcr_nkrylov=args.mg_nkrylov,
                                  delta_reliable=3e-4)
     ctx.wcl_invert(x, src, 12, mgb)  # warm-up (tuner, work space)
     mgb_s, binf = timed(lambda: ctx.wcl_invert(x, src, 12, mgb)[1])
-    line["mg_fgcr_batched"] = {"seconds": mgb_s, "coarse_steps": args.mg_coarse_steps,
+    line["mg_fgcr_batched"] = {"seconds": mgb_s, "coarse_steps": args.mg_coarse_steps, "nkrylov": args.mg_nkrylov,
                                "iters_per_rhs": float(np.mean([i["iters"] for i in binf])),
                                "reliable_updates_per_rhs": float(np.mean([i["reliable_updates"] for i in binf])),
                                "worst_true_residual": max(i["true_residual"] for i in binf)}
