@@ -123,3 +123,25 @@ def test_multigrid_twelve_source_solve_full_lattice_oracle_residual(problem):
     got = residual.true_residuals(gauge, xh, b, DIMS, KAPPA, CSW, t_boundary=-1)
     assert np.all(got <= 1e-10), got
     assert all(i["status"] == 0 for i in info), info
+
+
+def test_batched_multigrid_twelve_source_solve_full_lattice_oracle_residual(problem):
+    """The batched multigrid solver (all twelve point sources through one K-cycle, 8 coarse
+    steps, as bench.py --case mg runs it) at the benchmark's size: every true residual,
+    recomputed by the FP64 oracle over the whole lattice, is at most 1e-10."""
+    pkg, ctx, gauge = problem
+    starts = cuda(W.gaussian_fermion(DIMS, 500, nrhs=24))
+    ctx.wcl_mg_setup(starts, pkg.wcl_default_mg_params(coarse_maxiter=8))
+    del starts
+    b = np.stack([W.point_source(DIMS, s, c) for s in range(4) for c in range(3)])
+    x = cuda(np.zeros_like(b))
+    prm = pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=1e-10, gcr_nkrylov=20,
+                                 delta_reliable=3e-4)
+    _, info = ctx.wcl_invert(x, cuda(b), 12, prm)
+    xh = host(x)
+    del x
+    got = residual.true_residuals(gauge, xh, b, DIMS, KAPPA, CSW, t_boundary=-1)
+    assert np.all(got <= 1e-10), got
+    assert all(i["status"] == 0 for i in info), info
+    lib = np.array([i["true_residual"] for i in info])
+    assert np.all(np.abs(lib - got) <= 1e-3 * got + 1e-14), (lib, got)
