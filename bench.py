@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--mg-block", default="4,4,4,4", help="--case mg: block size per direction")
     ap.add_argument("--mg-nvec", type=int, default=24, help="--case mg: null vectors")
     ap.add_argument("--mg-nkrylov", type=int, default=20, help="--case mg: restart length of the outer FGCR")
+    ap.add_argument("--mg-smooth", default="2,2", help="--case mg: pre,post minimal-residual steps of the K-cycle")
     ap.add_argument("--mg-coarse-steps", type=int, default=8,
                     help="--case mg: coarse GCR steps of the batched K-cycle (solver fgcr_mg_batched)")
     ap.add_argument("--mg-single", type=int, default=1,
@@ -1024,7 +1025,9 @@ def run_mg_case(args):
     # all twelve right-hand sides at once: FGCR on M_hat preconditioned by the batched
     # K-cycle (a fixed number of coarse steps, every coefficient on the device)
     starts = torch.from_numpy(W.gaussian_fermion(dims, 500, nrhs=args.mg_nvec)).to(dev)
-    bprm = pkg.wcl_default_mg_params(block=block, nvec=args.mg_nvec, coarse_maxiter=args.mg_coarse_steps)
+    pre, post = (int(v) for v in args.mg_smooth.split(","))
+    bprm = pkg.wcl_default_mg_params(block=block, nvec=args.mg_nvec, coarse_maxiter=args.mg_coarse_steps, pre=pre,
+                                     post=post)
     ctx.wcl_mg_setup(starts, bprm)
     del starts
     mgb = pkg.wcl_default_params(solver="fgcr_mg_batched", sloppy="f32", tol=args.tol, gcr_nkrylov=args.mg_nkrylov,
@@ -1032,6 +1035,7 @@ def run_mg_case(args):
     ctx.wcl_invert(x, src, 12, mgb)  # warm-up (tuner, work space)
     mgb_s, binf = timed(lambda: ctx.wcl_invert(x, src, 12, mgb)[1])
     line["mg_fgcr_batched"] = {"seconds": mgb_s, "coarse_steps": args.mg_coarse_steps, "nkrylov": args.mg_nkrylov,
+                               "smoothing": [pre, post],
                                "iters_per_rhs": float(np.mean([i["iters"] for i in binf])),
                                "reliable_updates_per_rhs": float(np.mean([i["reliable_updates"] for i in binf])),
                                "worst_true_residual": max(i["true_residual"] for i in binf)}
