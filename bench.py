@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sloppy", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--delta", type=float, default=3e-4, help="reliable-update threshold")
     ap.add_argument("--check-every", type=int, default=2, help="iterations per graph replay / convergence check")
+    ap.add_argument("--sloppy-updates", type=int, default=0,
+                    help="16-bit inner solvers: updates above 10^-k ||b|| with the FP32 operator (0: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairs", type=int, default=2000, help="training pairs of --case compare")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of --case compare")
@@ -312,6 +314,9 @@ def run_ours(args, rank, world, local):
     x = torch.zeros_like(b)
     prm = pkg.wcl_default_params(solver="bicgstab", sloppy=args.sloppy, tol=TOL, check_every=args.check_every,
                                  delta_reliable=args.delta)
+    if args.sloppy_updates:
+        from paper_2411_08461_gb300.wcl import WCL_OPT_SLOPPY_UPDATES
+        ctx.wcl_set_option(WCL_OPT_SLOPPY_UPDATES, args.sloppy_updates)
 
     infos = None
     for _ in range(args.warmup):
@@ -424,7 +429,8 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": f"{args.sloppy} storage / f32 arithmetic / f64 residual", "data": "synthetic",
         "config": {"workload": WORKLOAD if dims == DIMS else WORKLOAD.replace("32^3x64", "x".join(map(str, dims))),
                    "lattice": "x".join(map(str, dims)), "nrhs": 12, "solver": "bicgstab even-odd",
-                   "sloppy": args.sloppy, "delta_reliable": args.delta, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "sloppy": args.sloppy, "delta_reliable": args.delta, "sloppy_updates": args.sloppy_updates,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set >> L2 (no flush needed)"},
         "solve": {"seconds": ms / 1e3, "iters_per_rhs": iters, "worst_true_residual": worst,
                   "reliable_updates": statistics.mean(i["reliable_updates"] for i in infos)},

@@ -359,6 +359,14 @@ typedef enum {
                             fewer terms need less shared memory per CTA and fewer MMAs.  The
                             network is a preconditioner of flexible GCR, whose true residual does
                             not depend on it. */
+  ,
+  WCL_OPT_SLOPPY_UPDATES = 11 /* k in 1..8: in a solve with an FP16 or BF16 inner solver and
+                                 double-float intermediate updates (outer WCL_DF64), a reliable
+                                 update made while the iterated residual is above 10^-k ||b||
+                                 evaluates b - M x with the FP32 operator, whose rounding is far
+                                 below the 16-bit recurrence's; later updates stay double-float
+                                 and the final ones IEEE FP64, so every reported residual is FP64.
+                                 0 (default): every intermediate update double-float. */
 } wcl_option;
 
 /* Set an option of ctx; unknown options give WCL_ERR_INVALID_ARG. */

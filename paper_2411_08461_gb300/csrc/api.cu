@@ -569,6 +569,12 @@ wcl_status wcl_set_option(wcl_ctx* c, int option, int value) {
         return WCL_OK;
       }
       break;
+    case WCL_OPT_SLOPPY_UPDATES:
+      if (value >= 0 && value <= 8) {
+        c->sloppy_updates = value;
+        return WCL_OK;
+      }
+      break;
   }
   set_error("wcl_set_option: unknown option %d or value %d", option, value);
   return WCL_ERR_INVALID_ARG;

@@ -381,6 +381,13 @@ __device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void*
 #pragma unroll
   for (int k = 0; k < 12; k++) v[k] = {double(d[k].re), double(d[k].im)};
 }
+template <>
+__device__ __forceinline__ void load_as_f64<F32>(cpx<double> v[12], const void* base, long stride, long i) {
+  cpx<float> d[12];
+  SpinorIO<F32>::load<false>(d, base, nullptr, stride, i);
+#pragma unroll
+  for (int k = 0; k < 12; k++) v[k] = {double(d[k].re), double(d[k].im)};
+}
 
 // Reliable update: r64 holds y = A_ee x_e - kappa D_eo x_o in precision Q (x_o the
 // reconstructed odd solution); r_e = b_e - y is formed in FP64 and equals the Schur
@@ -391,7 +398,8 @@ __device__ __forceinline__ void load_as_f64<DF64>(cpx<double> v[12], const void*
 // FP64 update (Q = F64: every update that may end a solve) are FP64 throughout; those
 // of a double-float update, which only decide whether an FP64 update follows, sum the
 // residual as rounded to the inner precision per site (FP32 pipes; GB300's FP64 rate
-// bounded this kernel) and add the per-site sums in FP64.
+// bounded this kernel) and add the per-site sums in FP64.  With Q = F32 (an early update of
+// a 16-bit inner solve, made with the FP32 operator) r64 is an FP32 field.
 template <int S, int Q>
 struct ResidualReplace {
   FieldRef r64, bhat, rS, rhat, ro;

@@ -68,6 +68,7 @@ struct wcl_ctx {
   bool prefetch_spinors = false; // untuned multi-RHS dslash: next hop's spinor prefetched in registers
   int tma_staging = 0;           // untuned multi-RHS FP32 dslash: links and clover staged by TMA
                                  // (1 persistent CTAs, 2 one CTA per tile)
+  int sloppy_updates = 0;        // 16-bit inner solves: updates above 10^-k ||b|| use the FP32 operator (0 off)
   int blas_block = 256;
   void* mg = nullptr;    // multigrid hierarchy (mg.cu), built by wcl_mg_setup
   void* stag = nullptr;  // staggered links and mass (stag.cu), loaded by wcl_load_staggered

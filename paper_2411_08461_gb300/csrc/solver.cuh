@@ -12,6 +12,8 @@
 //                    whole system b - M x; its even half (= b_hat - M_hat x_e)
 //                    replaces the sloppy residual, and ||b - M x|| / ||b|| decides
 //                    convergence -- so the last update is the final true-residual check.
+//                    With a 16-bit inner solver the early updates (residual above a
+//                    chosen 10^-k ||b||) may use the FP32 operator instead (option).
 // Every (lattice, rhs) slice keeps its own coefficients and is masked out of
 // every launch once it has converged.
 #pragma once
@@ -29,6 +31,7 @@ wcl_status ptc_apply(const std::vector<wcl_ctx*>& ctxs, int nrhs, const FieldRef
 template <int S>
 struct KrylovSolver {
   static constexpr int X = (S == F64) ? F64 : F32;  // precision of the sloppy solution accumulator
+  static constexpr int NMASK = 5;  // active, update, double-float, FP64, FP32 slice masks
   std::vector<wcl_ctx*> ctxs;
   wcl_ctx* c0 = nullptr;
   int nrhs = 0, nslot = 0;
@@ -36,11 +39,14 @@ struct KrylovSolver {
   bool cg = false;
   bool gcr = false;
   bool use_df = false;  // double-float operator for intermediate residual replacements
+  bool use_s32 = false;  // FP32 operator for the early updates of a 16-bit inner solve
+  double s32_level2 = 0;  // (10^-k)^2: an update above this ||r||^2 / ||b||^2 uses FP32
 
   FieldRef b_e, b_o, bhat, x, x_o, r64, tmp64;  // FP64
   FieldRef r, rhat, p, v, t, tmp;               // sloppy
   FieldRef xs;                                  // accumulator
   FieldRef x_df, bo_df;                         // double-float copies of x and b_o
+  FieldRef x32, o32, y32, bo32;                 // FP32 work fields of the early updates
   Scalars* d_sc = nullptr;
   Scalars* h_sc = nullptr;
   int* d_active = nullptr;
@@ -51,6 +57,8 @@ struct KrylovSolver {
   int* h_updf = nullptr;
   int* d_upd64 = nullptr;  // slices updated (or confirmed) in FP64
   int* h_upd64 = nullptr;
+  int* d_upd32 = nullptr;  // slices updated with the FP32 operator
+  int* h_upd32 = nullptr;
   double* d_part = nullptr;
   unsigned* d_cnt = nullptr;
   double* d_dpart = nullptr;   // dslash-epilogue partials
@@ -59,7 +67,7 @@ struct KrylovSolver {
   Batch bb;  // geometry of the BLAS / reduction launches
   int blk = 256;
 
-  std::vector<double> stop2, r2max;
+  std::vector<double> stop2, r2max, b2;
   std::vector<int> iters, updates, restarts, status;
 
   cudaGraphExec_t gexec = nullptr;
@@ -85,14 +93,21 @@ struct KrylovSolver {
       WCL_CHECK(ws_field(ctxs, "x_df", DF64, nrhs, &x_df));
       WCL_CHECK(ws_field(ctxs, "bo_df", DF64, nrhs, &bo_df));
     }
+    if (use_s32) {
+      WCL_CHECK(ws_field(ctxs, "u32_x", F32, nrhs, &x32));
+      WCL_CHECK(ws_field(ctxs, "u32_o", F32, nrhs, &o32));
+      WCL_CHECK(ws_field(ctxs, "u32_y", F32, nrhs, &y32));
+      WCL_CHECK(ws_field(ctxs, "u32_bo", F32, nrhs, &bo32));
+    }
     void* q;
     WCL_CHECK(ws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
     d_sc = static_cast<Scalars*>(q);
-    WCL_CHECK(ws_get(c0, "active", sizeof(int) * 4 * nslot, &q));
+    WCL_CHECK(ws_get(c0, "active", sizeof(int) * NMASK * nslot, &q));
     d_active = static_cast<int*>(q);
     d_upd = d_active + nslot;
     d_updf = d_active + 2 * nslot;
     d_upd64 = d_active + 3 * nslot;
+    d_upd32 = d_active + 4 * nslot;
     WCL_CHECK(ws_get(c0, "partials", sizeof(double) * nslot * RED_MAXCH * 2 * GCR_MAXK, &q));
     d_part = static_cast<double*>(q);
     WCL_CHECK(ws_get(c0, "counters", sizeof(unsigned) * nslot, &q));
@@ -104,11 +119,12 @@ struct KrylovSolver {
     d_dcnt = static_cast<unsigned*>(q);
     WCL_CHECK(hws_get(c0, "scalars", sizeof(Scalars) * nslot, &q));
     h_sc = static_cast<Scalars*>(q);
-    WCL_CHECK(hws_get(c0, "active", sizeof(int) * 4 * nslot, &q));
+    WCL_CHECK(hws_get(c0, "active", sizeof(int) * NMASK * nslot, &q));
     h_active = static_cast<int*>(q);
     h_upd = h_active + nslot;
     h_updf = h_active + 2 * nslot;
     h_upd64 = h_active + 3 * nslot;
+    h_upd32 = h_active + 4 * nslot;
     return WCL_OK;
   }
 
@@ -144,7 +160,7 @@ struct KrylovSolver {
     return WCL_OK;
   }
   wcl_status push_masks() {
-    WCL_CUDA(cudaMemcpyAsync(d_active, h_active, sizeof(int) * 4 * nslot, cudaMemcpyHostToDevice, c0->stream));
+    WCL_CUDA(cudaMemcpyAsync(d_active, h_active, sizeof(int) * NMASK * nslot, cudaMemcpyHostToDevice, c0->stream));
     return WCL_OK;
   }
 
@@ -222,6 +238,19 @@ struct KrylovSolver {
   // or double-float (~48-bit) for a replacement in the middle of a solve.
   wcl_status reliable_update(bool restart, int oprec, const int* mask) {
     const int bicg = (!cg && !restart) ? 1 : 0;
+    if constexpr (S == F16 || S == BF16) {
+      if (oprec == F32) {
+        // x += x_s in FP64, then with FP32 copies: x_o = A_oo^-1 (b_o + kappa D_oe x_e),
+        // (M x)_e = A_ee x_e - kappa D_eo x_o, and r = b_e - (M x)_e formed in FP64
+        WCL_CHECK(map(AddInto64<X>{x, xs}, mask));
+        WCL_CHECK(convert(ctxs, F32, F64, nrhs, x32, x, mask));
+        WCL_CHECK(dslash(ctxs, F32, nrhs, o32, x32, &bo32, 1, false, CL_AINV, CL_NONE, C_KAPPA, C_ONE, mask));
+        WCL_CHECK(dslash(ctxs, F32, nrhs, y32, o32, &x32, 0, false, CL_NONE, CL_A, C_MKAPPA, C_ONE, mask));
+        WCL_CHECK(reduce<4>(ResidualReplace<S, F32>{y32, b_e, r, rhat, FieldRef{}, bicg}, mask));
+        if (restart) WCL_CHECK(restart_krylov(mask));
+        return WCL_OK;
+      }
+    }
     if (oprec == DF64) {
       // double-float operator on double-float copies; x_o and r64 hold double-float
       // values until ResidualReplace turns r64 into the FP64 residual.  The odd
@@ -248,9 +277,9 @@ struct KrylovSolver {
   // status and every reported true residual comes from an FP64 evaluation.
   // On return h_upd64[s] marks the slices whose aux[] holds an FP64 result.
   wcl_status update_round(bool restart) {
-    bool any_df = false, any_64 = false;
+    bool any_df = false, any_64 = false, any_32 = false;
     for (int s = 0; s < nslot; s++) {
-      h_updf[s] = h_upd64[s] = 0;
+      h_updf[s] = h_upd64[s] = h_upd32[s] = 0;
       if (!h_upd[s]) continue;
       const double r2 = h_sc[s].r2;
       const bool ending = r2 <= stop2[s] || iters[s] >= prm.maxiter || (h_sc[s].flags & 1) || !(r2 == r2) ||
@@ -258,12 +287,16 @@ struct KrylovSolver {
       if (ending) {
         h_upd64[s] = 1;
         any_64 = true;
+      } else if (use_s32 && r2 > s32_level2 * b2[s]) {
+        h_upd32[s] = 1;
+        any_32 = true;
       } else {
         h_updf[s] = 1;
         any_df = true;
       }
     }
     WCL_CHECK(push_masks());
+    if (any_32) WCL_CHECK(reliable_update(restart, F32, d_upd32));
     if (any_df) WCL_CHECK(reliable_update(restart, DF64, d_updf));
     if (any_64) WCL_CHECK(reliable_update(restart, F64, d_upd64));
     WCL_CHECK(sync_scalars());
@@ -286,6 +319,7 @@ struct KrylovSolver {
       profile_sync();
       for (int s = 0; s < nslot; s++) h_updf[s] = 0;
     }
+    for (int s = 0; s < nslot; s++) h_upd32[s] = 0;
     return WCL_OK;
   }
 
@@ -460,15 +494,18 @@ struct KrylovSolver {
     // Intermediate residual replacements of a mixed-precision solve use the
     // double-float operator (FP32 pipes); every final one is IEEE FP64.
     use_df = S != F64 && prm.outer == WCL_DF64;
+    use_s32 = (S == F16 || S == BF16) && use_df && c0->sloppy_updates > 0 && !gcr;
+    if (use_s32) s32_level2 = std::pow(10.0, -2.0 * c0->sloppy_updates);
     WCL_CHECK(alloc());
     stop2.assign(nslot, 0);
+    b2.assign(nslot, 0);
     r2max.assign(nslot, 0);
     iters.assign(nslot, 0);
     updates.assign(nslot, 0);
     restarts.assign(nslot, 0);
     status.assign(nslot, WCL_OK);
     WCL_CUDA(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * nslot, c0->stream));
-    for (int s = 0; s < nslot; s++) h_active[s] = 1, h_upd[s] = h_updf[s] = h_upd64[s] = 0;
+    for (int s = 0; s < nslot; s++) h_active[s] = 1, h_upd[s] = h_updf[s] = h_upd64[s] = h_upd32[s] = 0;
     WCL_CHECK(push_masks());
     WCL_CUDA(cudaMemsetAsync(c0->d_flags, 0, sizeof(int), c0->stream));
 
@@ -488,6 +525,7 @@ struct KrylovSolver {
     // independent of how b_hat was rounded.  It is therefore formed with the
     // sloppy operator (v, t, tmp and r are free until the first iteration).
     if (use_df) WCL_CHECK(convert(ctxs, DF64, F64, nrhs, bo_df, b_o, nullptr));
+    if (use_s32) WCL_CHECK(convert(ctxs, F32, F64, nrhs, bo32, b_o, nullptr));
     if (S != F64) {
       WCL_CHECK(convert(ctxs, S, F64, nrhs, v, b_o, nullptr));
       WCL_CHECK(convert(ctxs, S, F64, nrhs, t, b_e, nullptr));
@@ -520,10 +558,11 @@ struct KrylovSolver {
     const double safety = 0.81;  // aim 10% below the target on the Schur residual
     int nactive = 0;
     for (int s = 0; s < nslot; s++) {
-      const double b2 = h_sc[s].aux[2];
-      stop2[s] = tol2 * b2 * safety;
+      const double bb = h_sc[s].aux[2];
+      b2[s] = bb;
+      stop2[s] = tol2 * bb * safety;
       r2max[s] = h_sc[s].aux[1];
-      if (!(b2 > 0.0)) {
+      if (!(bb > 0.0)) {
         h_active[s] = 0;  // zero source: x = 0 exactly
       } else {
         nactive++;

@@ -33,6 +33,7 @@ WCL_OPT_PAIRED_RHS = 7
 WCL_OPT_PREFETCH_SPINORS = 8
 WCL_OPT_TMA_STAGING = 9
 WCL_OPT_PTC_SPLIT = 10
+WCL_OPT_SLOPPY_UPDATES = 11
 PTC_CHANNELS = (1, 4, 4, 4, 1)
 
 

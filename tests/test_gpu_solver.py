@@ -63,6 +63,31 @@ def test_mixed_precision_reaches_1e10(pkg, sloppy, solver, outer):
     ctx.close()
 
 
+@pytest.mark.parametrize("sloppy,k", [("f16", 4), ("bf16", 3), ("f16", 0)])
+def test_fp32_early_updates_of_16bit_solves(pkg, sloppy, k):
+    """16-bit inner solver whose updates above 10^-k ||b|| evaluate b - M x with the FP32
+    operator (k = 0: every intermediate update double-float): 12 RHS, every solution's
+    true residual recomputed by the oracle, and the library's FP64 value agrees with it."""
+    from paper_2411_08461_gb300.wcl import WCL_OPT_SLOPPY_UPDATES
+    dims = (8, 8, 8, 16)
+    gauge = W.gauge_links(dims, 0.3, 3)
+    ctx = pkg.Context(dims)
+    ctx.wcl_load_gauge(cuda(gauge), 0.1235, 1.0)
+    ctx.wcl_set_option(WCL_OPT_SLOPPY_UPDATES, k)
+    b = np.stack([W.point_source(dims, s, c) for s in range(4) for c in range(3)])
+    x = cuda(np.zeros_like(b))
+    _, info = ctx.wcl_invert(x, cuda(b), 12, pkg.wcl_default_params(sloppy=sloppy, tol=1e-10, delta_reliable=0.01,
+                                                                    check_every=2))
+    op = dirac.from_qdp_problem(gauge, dims, 0.1235, 1.0)
+    xh = host(x)
+    for j in range(12):
+        tr = _oracle_true_residual(op, xh[j], b[j])
+        assert tr <= 1e-10, (j, tr, info[j])
+        assert info[j]["status"] == 0 and info[j]["reliable_updates"] >= 2
+        assert abs(tr - info[j]["true_residual"]) <= 1e-3 * tr, (tr, info[j])
+    ctx.close()
+
+
 def test_twelve_spin_colour_sources(pkg):
     dims = (4, 4, 4, 8)
     gauge = W.gauge_links(dims, 0.3, 2)
