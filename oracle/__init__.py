@@ -30,10 +30,12 @@ The oracle is a plain, slow, direct transcription of the definitions:
 * ``residual`` -- the true residual ||b - M x|| / ||b|| of Eq. 5's operator evaluated one
                  slab of timeslices at a time (optionally in spawned processes), for
                  lattices too large for the whole-array evaluation.
+* ``force``   -- the HMC fermion force of the two-flavour even-odd clover action (with
+                 the odd-site clover determinant) and the action itself (Sec. IV).
 
 Everything is complex128 and operates on whole-lattice arrays in
 lexicographic order (Lt, Lz, Ly, Lx, ...), converting to and from the QDP
 layout at the edges.  Which pins check each function is stated in its
 docstring; functions without a pin say "parity unpinned".
 """
-from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered, hisq, residual  # noqa: F401
+from . import gamma, lattice, dirac, solvers, ptc, contract, multigrid, spectrum, staggered, hisq, residual, force  # noqa: F401
