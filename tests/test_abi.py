@@ -55,6 +55,23 @@ def test_host_only_calls_without_a_gpu():
     assert b"even" in lib.wcl_last_error()
 
 
+def test_force_and_batched_multigrid_argument_checks_without_a_gpu():
+    """The clover force and the batched multigrid cycle refuse null handles and pointers,
+    and the cycle a right-hand-side count outside 1..12, before any device call."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2411_08461_gb300 import wcl
+
+    lib = wcl.load_library()
+    assert lib.wcl_clover_force(None, None, None, 1) == 1
+    assert b"null" in lib.wcl_last_error()
+    assert lib.wcl_mg_cycle_batched(None, None, None, 1) == 1
+    assert lib.wcl_mg_cycle_batched(None, None, None, 13) == 1
+    assert b"nrhs" in lib.wcl_last_error()
+    assert lib.wcl_set_option(None, wcl.WCL_OPT_SLOPPY_UPDATES, 3) == 1
+
+
 def test_gamma_and_kappa_helpers_without_a_gpu():
     """wcl_gamma reproduces the oracle's independently written Gamma(n) for all 16 n,
     and wcl_kappa_from_mass the isotropic kappa relation; both are host-only calls."""
